@@ -1,0 +1,195 @@
+/*
+ * matexpre.h -- C ABI of the GB300 (sm_103a) MatExPre library.
+ *
+ * MatExPre (arXiv 2506.03617) preconditions the finite-difference Helmholtz
+ * operator with PML and complex shift through matrix-exponential actions:
+ * Algorithm 1 computes r <- psi_1(i t A_s) r and then solves
+ * (I - exp(i t A_s)) w = r with GMRES to a relative tolerance fprtol; outer
+ * flexible GMRES uses w as the preconditioned direction (Sec. 3.4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Layout.  A grid vector is complex128, interleaved (re, im), one value per
+ *    unknown, x fastest: index = i + n_x (j + n_y k).  Axis d holds
+ *    n_d = N_d + 2 npml unknowns; unknown j sits at x_j = (j - npml + 1/2) h and
+ *    the Dirichlet zero values sit at j = -1 and j = n_d.
+ *  Memory.  Unless a name ends in _host, vector arguments are DEVICE pointers
+ *    on the problem's device, 16-byte aligned, owned by the caller, and must
+ *    not alias each other.  The library owns the medium copy, the PML profiles
+ *    and the Krylov workspace; all are released by mxp_destroy.
+ *  Streams.  All work is enqueued on the stream given to mxp_create (NULL = the
+ *    legacy default stream).  Calls that return statistics or decide on
+ *    convergence synchronise that stream.
+ *  Errors.  Every call returns an mxp_status; no exception crosses the ABI.
+ *    On failure mxp_last_error() returns a thread-local message.  Invalid
+ *    arguments are rejected before any device work is enqueued.
+ *  Threads.  A problem handle may be used by one host thread at a time.
+ */
+#ifndef MATEXPRE_H
+#define MATEXPRE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MXP_OK = 0,
+    MXP_EINVAL = 1,       /* invalid argument (sizes, NULL, non-finite values) */
+    MXP_ENOMEM = 2,       /* device or host allocation failed */
+    MXP_ECUDA = 3,        /* a CUDA runtime call failed */
+    MXP_ENOCONV = 4,      /* iteration limit reached before the tolerance */
+    MXP_EBREAKDOWN = 5,   /* Krylov breakdown that is not a lucky one */
+    MXP_ENAN = 6,         /* NaN or Inf met in a residual */
+    MXP_ETIMEOUT = 7      /* a bounded device-side wait gave up */
+} mxp_status;
+
+/* Precision of the matrix-exponential actions inside the MatExPre apply.
+ * The Krylov bases, dot products, Hessenberg/Givens algebra of both GMRES
+ * levels and every residual check stay complex128/FP64 in all modes. */
+typedef enum {
+    MXP_C128 = 0,         /* complex128 storage and arithmetic */
+    MXP_C64 = 1,          /* complex64 storage and arithmetic */
+    MXP_BF16S = 2         /* bfloat16 storage of the recurrence vectors and
+                             float storage of the medium, float arithmetic */
+} mxp_precision;
+
+/* Grid: dim = 2 or 3; n_interior[d] = N_d interior cells (>= 1) for d < dim;
+ * npml = PML cells on each side (>= 0); h = mesh size (> 0), normally
+ * 1 / max_d N_d (the paper scales the largest interior extent to 1, Sec. 4). */
+typedef struct {
+    int dim;
+    int64_t n_interior[3];
+    int npml;
+    double h;
+} mxp_grid;
+
+/* Method parameters (Sec. 3.3-3.4, Sec. 4).
+ *  omega      angular frequency (> 0)
+ *  c_pml      PML strength C_pml of Eq. pml-1d-s (>= 0; paper: 20)
+ *  shift_s    complex shift s of A_s = A + i omega^2 s diag(1/c^2) (>= 0)
+ *  t          time length of the exponential integrators (> 0)
+ *  fprtol     inner GMRES relative tolerance of Algorithm 1 (0 < fprtol < 1)
+ *  exp_tol    truncation tolerance of each exp / psi_1 action (0 < exp_tol < 1)
+ *  inner_restart  inner GMRES restart length (1 .. 64)
+ *  inner_maxit    cap on inner iterations per apply (>= 1)
+ *  inner_fixed    if > 0: exactly this many inner iterations, tolerance
+ *                 ignored (makes the apply a fixed linear map)
+ *  prec       precision of the exp / psi_1 actions
+ *  theta_max  largest sub-step norm ||t A_s'||/S used by the Taylor actions
+ *             (0 = default: 6 for MXP_C128, 4 otherwise)
+ *  fuse_k     Taylor steps fused per pass by the tiled kernels (0 = automatic) */
+typedef struct {
+    double omega, c_pml, shift_s, t, fprtol, exp_tol;
+    int inner_restart, inner_maxit, inner_fixed;
+    mxp_precision prec;
+    double theta_max;
+    int fuse_k;
+} mxp_params;
+
+/* Statistics of one MatExPre apply (Algorithm 1). */
+typedef struct {
+    int inner_iters;          /* inner GMRES iterations */
+    int converged;            /* inner tolerance met (1) or not (0) */
+    double inner_relres;      /* final inner residual estimate / ||psi_1 r|| */
+    int64_t stencil_passes;   /* Taylor steps (stencil sweeps) executed */
+    int64_t pt_updates;       /* stencil_passes * unknowns */
+} mxp_apply_stats;
+
+/* Outer solve options.  rtol: stop when ||b - A x|| <= rtol ||b|| (true
+ * residual, unshifted A); restart: FGMRES restart (1 .. 64); maxit: cap on
+ * outer iterations; x0_given: nonzero = x holds the initial guess on entry,
+ * zero = start from x = 0. */
+typedef struct {
+    double rtol;
+    int restart;
+    int maxit;
+    int x0_given;
+} mxp_solve_opts;
+
+typedef struct {
+    int outer_iters;
+    int inner_iters_total;
+    int converged;
+    double true_relres;        /* ||b - A x|| / ||b|| at return */
+    double est_relres;         /* last FGMRES estimate / ||b|| */
+    int64_t stencil_passes;    /* all stencil sweeps (actions + operator) */
+    int64_t pt_updates;        /* sum over sweeps of the unknowns touched */
+    double seconds;            /* wall time of the call (host clock) */
+} mxp_solve_stats;
+
+typedef struct mxp_problem mxp_problem;   /* opaque, library-owned */
+
+/* Create a problem on `device` with wave speed c_host (host array of
+ * prod_d n_d doubles, x fastest, every value finite and > 0).  Parameters
+ * start at the paper defaults for ppw 10 w.r.t. min c (mxp_default_params).
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ * Follows the problem statement of Eq. helmholtz and Eq. pml-1d-s. */
+mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device,
+                      void *cuda_stream, mxp_problem **out);
+
+/* Fill *p with the paper's rules for a grid whose slowest speed is c_min and
+ * `ppw` points per slowest wavelength: omega = 2 pi c_min / (ppw h),
+ * freq = 1/(ppw h), s = 1/freq, t = 40 h^2 (0.4/freq^2 at ppw 10), C_pml 20,
+ * fprtol 0.08, exp_tol 1e-12, restart 30 (Sec. 4). */
+mxp_status mxp_default_params(const mxp_grid *grid, double c_min, double ppw,
+                              mxp_params *p);
+
+/* Replace the problem's parameters (NULL restores the defaults). */
+mxp_status mxp_set_params(mxp_problem *prob, const mxp_params *p);
+mxp_status mxp_get_params(const mxp_problem *prob, mxp_params *p);
+
+/* y = A x (shifted = 0) or y = A_s x (shifted = 1), complex128.
+ * (A x)_p = sum_d a_d [b_d+ (x_{p+e_d} - x_p) - b_d- (x_p - x_{p-e_d})] / h^2
+ *           + omega^2 (1 + i s [shifted]) / c_p^2 x_p, with a_d = 1/s_d at the
+ * node and b_d+- = 1/s_d at the half nodes (Eq. helmholtz, Eq. pml-1d-s,
+ * Sec. 3.4).  Always computed in FP64. */
+mxp_status mxp_apply_operator(mxp_problem *prob, int shifted, const void *x_dev,
+                              void *y_dev);
+
+/* y = exp(i t A_s) x (which = 0) or y = psi_1(i t A_s) x (which = 1)
+ * (Def. psi), in the problem's precision; x and y are complex128.
+ * passes_out (nullable) receives the number of stencil sweeps. */
+mxp_status mxp_apply_phi(mxp_problem *prob, int which, const void *x_dev, void *y_dev,
+                         int64_t *passes_out);
+
+/* w = MatExPre(r): Algorithm 1 with the problem's parameters.  st nullable.
+ * Returns MXP_OK also when the inner GMRES stopped at inner_maxit (st->converged
+ * tells which); MXP_ENAN if a residual became non-finite. */
+mxp_status mxp_apply_matexpre(mxp_problem *prob, const void *r_dev, void *w_dev,
+                              mxp_apply_stats *st);
+
+/* Solve A x = b (unshifted A) by FGMRES(restart) preconditioned on the right
+ * by MatExPre (Sec. 3.4).  Returns MXP_ENOCONV when maxit is reached first
+ * (x then holds the last iterate).  st nullable.  b = -f for Eq. helmholtz. */
+mxp_status mxp_solve(mxp_problem *prob, const void *b_dev, void *x_dev,
+                     const mxp_solve_opts *opts, mxp_solve_stats *st);
+
+/* mxp_solve with HOST buffers: copies b to the device, solves, copies x back
+ * (x_host also supplies the initial guess when opts->x0_given). */
+mxp_status mxp_solve_host(mxp_problem *prob, const void *b_host, void *x_host,
+                          const mxp_solve_opts *opts, mxp_solve_stats *st);
+
+/* Many right-hand sides over several problems in one call.  Right-hand side r
+ * belongs to problem probs[prob_of_rhs[r]]; b_dev[r], x_dev[r] are its vectors
+ * on that problem's device.  All problems must share one device and stream.
+ * Sources of a problem are solved together: their stencil sweeps run as one
+ * launch over the batch.  per_rhs (nullable) has nrhs entries. */
+mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs,
+                           const int *prob_of_rhs, const void *const *b_dev,
+                           void *const *x_dev, const mxp_solve_opts *opts,
+                           mxp_solve_stats *per_rhs);
+
+/* Number of unknowns prod_d n_d of the problem. */
+int64_t mxp_num_unknowns(const mxp_problem *prob);
+
+void mxp_destroy(mxp_problem *prob);
+const char *mxp_status_string(mxp_status s);
+const char *mxp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MATEXPRE_H */

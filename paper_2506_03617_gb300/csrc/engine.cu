@@ -1,0 +1,839 @@
+// Solver engine and C ABI of libmatexpre: problem setup (medium, PML profiles,
+// complex shift), the exp / psi_1 actions as shifted Taylor-Horner sweeps,
+// Algorithm 1 (inner GMRES on (I - exp(i t A_s)) w = psi_1(i t A_s) r) and the
+// outer flexible GMRES (Sec. 3.4).
+//
+// Matrix functions (Def. psi).  With a real shift mu, M = i t A_s
+// = i t mu I + M', M' = i t (A_s - mu I), and exp(M) = e^{i t mu} exp(M').
+// psi_1(M) v is the first block of exp(B)[0; 1] for the augmented matrix
+// B = [[M, v], [0, 0]]; shifting B by i t mu leaves the scalar row as
+// e^{-i t mu tau}, so both actions become exp of a shifted (augmented) matrix
+// applied over S sub-steps, each a degree-m Taylor polynomial in Horner form:
+//   p <- y + (X p + gamma_k v) / k,  k = m .. 1,  X = M'/S,
+// where gamma_k carries the scalar (augmented) component.  mu minimises the
+// row-sum norm bound nu = ||t (A_s - mu I)||_inf; (S, m) minimise S*m subject
+// to S (nu/S)^(m+1)/(m+1)! e^(nu/S) <= exp_tol and nu/S <= theta_max.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mxp_internal.h"
+
+using namespace mxp;
+using cd = std::complex<double>;
+
+static thread_local std::string g_last_error;
+
+static mxp_status fail(mxp_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? MXP_ENOMEM : MXP_ECUDA,           \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                \
+    } while (0)
+
+#define CKS(expr)                                \
+    do {                                         \
+        mxp_status s_ = (expr);                  \
+        if (s_ != MXP_OK) return s_;             \
+    } while (0)
+
+struct TaylorPlan {
+    int S = 1;      // sub-steps
+    int m = 1;      // Taylor degree per sub-step
+    double nu = 0;  // norm bound used
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d)
+    {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct Arnoldi {
+    double2 *V = nullptr;     // (R+1) vectors
+    double2 *Z = nullptr;     // R vectors (flexible variant only)
+    HessState hs{};
+    double2 *tmpcol = nullptr;
+    int R = 0;
+};
+
+struct mxp_problem {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    mxp_grid grid{};
+    Geom geom{};
+    int64_t ntot = 0;
+    double cmin = 0, cmax = 0;
+    mxp_params prm{};
+    // device data
+    double *c_dev = nullptr;
+    double *kappa64 = nullptr;
+    float *kappa32 = nullptr;
+    double2 *coef64 = nullptr;
+    float2 *coef32 = nullptr;
+    std::vector<double2> coef_host;   // [3][3][nmax]
+    // shift and plans
+    double mu = 0;
+    TaylorPlan plan_exp, plan_psi;
+    // workspace
+    void *hb[4] = {nullptr, nullptr, nullptr, nullptr};   // 16 bytes per unknown each
+    double2 *rt = nullptr, *tmp = nullptr, *tmp2 = nullptr;
+    double2 *bdev = nullptr, *xdev = nullptr;
+    Arnoldi inner, outer;
+    KrylovScratch ks{};
+    double *host_scal = nullptr;   // pinned, 8 doubles
+    // counters
+    int64_t passes = 0;
+};
+
+// ------------------------------------------------------------------ helpers
+
+static cd inv_stretch(const mxp_problem *P, int d, double x)
+{
+    const int p = P->grid.npml;
+    if (p == 0) return 1.0;
+    const double h = P->grid.h;
+    const double L = (double)P->grid.n_interior[d] * h;
+    const double delta = p * h;
+    double dist = 0.0;
+    if (x < 0.0) dist = -x;
+    if (x > L) dist = x - L;
+    const double r = dist / delta;
+    const cd s(1.0, P->prm.c_pml / (delta * P->prm.omega) * r * r);
+    return 1.0 / s;
+}
+
+static void build_coef_host(mxp_problem *P)
+{
+    const int nm = P->geom.nmax;
+    const double h = P->grid.h, ih2 = 1.0 / (h * h);
+    P->coef_host.assign((size_t)9 * nm, make_double2(0, 0));
+    for (int d = 0; d < P->grid.dim; ++d) {
+        for (int i = 0; i < P->geom.n[d]; ++i) {
+            const double x = ((double)i - P->grid.npml + 0.5) * h;
+            const cd a = inv_stretch(P, d, x);
+            const cd bp = inv_stretch(P, d, x + 0.5 * h);
+            const cd bm = inv_stretch(P, d, x - 0.5 * h);
+            const cd wp = a * bp * ih2, wm = a * bm * ih2, wc = wp + wm;
+            P->coef_host[(size_t)(3 * d + 0) * nm + i] = make_double2(wp.real(), wp.imag());
+            P->coef_host[(size_t)(3 * d + 1) * nm + i] = make_double2(wm.real(), wm.imag());
+            P->coef_host[(size_t)(3 * d + 2) * nm + i] = make_double2(wc.real(), wc.imag());
+        }
+    }
+}
+
+// Representative indices of axis d: every PML index plus one interior index
+// (interior nodes share identical coefficients).
+static std::vector<int> axis_classes(const mxp_problem *P, int d)
+{
+    std::vector<int> out;
+    const int n = P->geom.n[d], p = P->grid.npml;
+    for (int i = 0; i < n; ++i) {
+        const bool pml = (i < p) || (i >= n - p);
+        if (pml || i == p) out.push_back(i);
+    }
+    return out;
+}
+
+// nu(mu) = t * max over (axis classes, kappa in {kmin, kmax}) of
+//          sum_d (|wp_d| + |wm_d|) + |kappa (1 + i s) - sum_d wc_d - mu|.
+// This bounds ||t (A_s - mu I)||_inf from above (the medium may vary inside a
+// class; |.| is convex in kappa so its endpoints bound it).
+struct NormTable {
+    std::vector<double> off;    // per combination
+    std::vector<cd> wcs;        // per combination
+};
+
+static NormTable norm_table(const mxp_problem *P)
+{
+    NormTable T;
+    const int nm = P->geom.nmax;
+    std::vector<int> cls[3];
+    for (int d = 0; d < 3; ++d) cls[d] = (d < P->grid.dim) ? axis_classes(P, d) : std::vector<int>{-1};
+    for (int i0 : cls[0])
+        for (int i1 : cls[1])
+            for (int i2 : cls[2]) {
+                int idx[3] = {i0, i1, i2};
+                double off = 0;
+                cd wcs = 0;
+                for (int d = 0; d < P->grid.dim; ++d) {
+                    const double2 wp = P->coef_host[(size_t)(3 * d) * nm + idx[d]];
+                    const double2 wm = P->coef_host[(size_t)(3 * d + 1) * nm + idx[d]];
+                    const double2 wc = P->coef_host[(size_t)(3 * d + 2) * nm + idx[d]];
+                    off += std::hypot(wp.x, wp.y) + std::hypot(wm.x, wm.y);
+                    wcs += cd(wc.x, wc.y);
+                }
+                T.off.push_back(off);
+                T.wcs.push_back(wcs);
+            }
+    return T;
+}
+
+static double nu_of_mu(const mxp_problem *P, const NormTable &T, double mu)
+{
+    const double w2 = P->prm.omega * P->prm.omega;
+    const double kap[2] = {w2 / (P->cmax * P->cmax), w2 / (P->cmin * P->cmin)};
+    const cd z(1.0, P->prm.shift_s);
+    double best = 0;
+    for (size_t c = 0; c < T.off.size(); ++c)
+        for (double k : kap) {
+            const double v = T.off[c] + std::abs(k * z - T.wcs[c] - mu);
+            if (v > best) best = v;
+        }
+    return P->prm.t * best;
+}
+
+static TaylorPlan make_plan(double nu, double tol, double theta_max, int kmult)
+{
+    TaylorPlan best;
+    best.nu = nu;
+    if (!(nu > 0)) {
+        best.S = 1;
+        best.m = kmult;
+        return best;
+    }
+    const int Smin = std::max(1, (int)std::ceil(nu / theta_max));
+    long best_cost = -1;
+    for (int S = Smin; S <= 4 * Smin + 8; ++S) {
+        const double th = nu / S;
+        const double lt = std::log(tol);
+        int m = 1;
+        for (; m < 400; ++m) {
+            const double lg = std::log((double)S) + (m + 1) * std::log(th) - std::lgamma(m + 2.0) + th;
+            if (lg <= lt) break;
+        }
+        if (kmult > 1) m = ((m + kmult - 1) / kmult) * kmult;
+        const long cost = (long)m * S;
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best.S = S;
+            best.m = m;
+        }
+    }
+    return best;
+}
+
+static int effective_fuse(const mxp_problem *P)
+{
+    if (P->prm.fuse_k > 0) return P->prm.fuse_k;
+    return 1;
+}
+
+static void update_plans(mxp_problem *P)
+{
+    const NormTable T = norm_table(P);
+    // golden-section search for the mu minimising the convex nu(mu)
+    const double w2 = P->prm.omega * P->prm.omega;
+    double lo = -1e300, hi = 1e300;
+    for (size_t c = 0; c < T.wcs.size(); ++c) {
+        const double k1 = w2 / (P->cmax * P->cmax), k2 = w2 / (P->cmin * P->cmin);
+        const double r1 = k1 - T.wcs[c].real(), r2 = k2 - T.wcs[c].real();
+        lo = (lo == -1e300) ? std::min(r1, r2) : std::min(lo, std::min(r1, r2));
+        hi = (hi == 1e300) ? std::max(r1, r2) : std::max(hi, std::max(r1, r2));
+    }
+    const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+    double a = lo, b = hi;
+    double x1 = b - gr * (b - a), x2 = a + gr * (b - a);
+    double f1 = nu_of_mu(P, T, x1), f2 = nu_of_mu(P, T, x2);
+    for (int it = 0; it < 200 && (b - a) > 1e-12 * (std::abs(a) + std::abs(b) + 1); ++it) {
+        if (f1 < f2) { b = x2; x2 = x1; f2 = f1; x1 = b - gr * (b - a); f1 = nu_of_mu(P, T, x1); }
+        else { a = x1; x1 = x2; f1 = f2; x2 = a + gr * (b - a); f2 = nu_of_mu(P, T, x2); }
+    }
+    P->mu = 0.5 * (a + b);
+    const double nu = nu_of_mu(P, T, P->mu);
+    double theta = P->prm.theta_max;
+    if (!(theta > 0)) theta = (P->prm.prec == MXP_C128) ? 6.0 : 4.0;
+    const int km = effective_fuse(P);
+    P->plan_exp = make_plan(nu, P->prm.exp_tol, theta, km);
+    const double nu_aug = std::max(nu, std::abs(P->prm.t * P->mu));
+    P->plan_psi = make_plan(nu_aug, P->prm.exp_tol * 0.1, theta, km);
+}
+
+static mxp_status upload_coefs(mxp_problem *P)
+{
+    build_coef_host(P);
+    const size_t cnt = P->coef_host.size();
+    std::vector<float2> c32(cnt);
+    for (size_t i = 0; i < cnt; ++i) c32[i] = make_float2((float)P->coef_host[i].x, (float)P->coef_host[i].y);
+    CK(cudaMemcpyAsync(P->coef64, P->coef_host.data(), cnt * sizeof(double2), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->coef32, c32.data(), cnt * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
+    compute_kappa(P->c_dev, P->prm.omega, P->kappa64, P->kappa32, P->ntot, P->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(P->stream));
+    return MXP_OK;
+}
+
+static mxp_status validate_params(const mxp_params *p)
+{
+    auto fin = [](double v) { return std::isfinite(v); };
+    if (!fin(p->omega) || p->omega <= 0) return fail(MXP_EINVAL, "omega must be finite and > 0");
+    if (!fin(p->c_pml) || p->c_pml < 0) return fail(MXP_EINVAL, "c_pml must be finite and >= 0");
+    if (!fin(p->shift_s) || p->shift_s < 0) return fail(MXP_EINVAL, "shift_s must be finite and >= 0");
+    if (!fin(p->t) || p->t <= 0) return fail(MXP_EINVAL, "t must be finite and > 0");
+    if (!fin(p->fprtol) || p->fprtol <= 0 || p->fprtol >= 1) return fail(MXP_EINVAL, "fprtol must lie in (0, 1)");
+    if (!fin(p->exp_tol) || p->exp_tol <= 0 || p->exp_tol >= 1) return fail(MXP_EINVAL, "exp_tol must lie in (0, 1)");
+    if (p->inner_restart < 1 || p->inner_restart > 64) return fail(MXP_EINVAL, "inner_restart must lie in [1, 64]");
+    if (p->inner_maxit < 1) return fail(MXP_EINVAL, "inner_maxit must be >= 1");
+    if (p->inner_fixed < 0) return fail(MXP_EINVAL, "inner_fixed must be >= 0");
+    if (p->prec != MXP_C128 && p->prec != MXP_C64 && p->prec != MXP_BF16S) return fail(MXP_EINVAL, "unknown precision");
+    if (!fin(p->theta_max) || p->theta_max < 0 || p->theta_max > 30) return fail(MXP_EINVAL, "theta_max must lie in [0, 30]");
+    if (p->fuse_k < 0 || p->fuse_k > 16) return fail(MXP_EINVAL, "fuse_k must lie in [0, 16]");
+    return MXP_OK;
+}
+
+static void free_arnoldi(Arnoldi &a)
+{
+    cudaFree(a.V); cudaFree(a.Z); cudaFree(a.hs.H); cudaFree(a.hs.cs); cudaFree(a.hs.sn);
+    cudaFree(a.hs.g); cudaFree(a.hs.y); cudaFree(a.hs.scal); cudaFree(a.tmpcol);
+    a = Arnoldi{};
+}
+
+static mxp_status ensure_arnoldi(mxp_problem *P, Arnoldi &a, int R, bool flexible)
+{
+    if (a.V && a.R >= R && (!flexible || a.Z)) return MXP_OK;
+    free_arnoldi(a);
+    const int64_t n = P->ntot;
+    CK(cudaMalloc(&a.V, (size_t)(R + 1) * n * sizeof(double2)));
+    if (flexible) CK(cudaMalloc(&a.Z, (size_t)R * n * sizeof(double2)));
+    CK(cudaMalloc(&a.hs.H, (size_t)(R + 1) * R * sizeof(double2)));
+    CK(cudaMalloc(&a.hs.cs, R * sizeof(double)));
+    CK(cudaMalloc(&a.hs.sn, R * sizeof(double2)));
+    CK(cudaMalloc(&a.hs.g, (R + 1) * sizeof(double2)));
+    CK(cudaMalloc(&a.hs.y, R * sizeof(double2)));
+    CK(cudaMalloc(&a.hs.scal, 8 * sizeof(double)));
+    CK(cudaMalloc(&a.tmpcol, (R + 1) * sizeof(double2)));
+    CK(cudaMemsetAsync(a.hs.H, 0, (size_t)(R + 1) * R * sizeof(double2), P->stream));
+    a.hs.R = R;
+    a.R = R;
+    return MXP_OK;
+}
+
+static mxp_status ensure_base(mxp_problem *P)
+{
+    const int64_t n = P->ntot;
+    for (int i = 0; i < 4; ++i)
+        if (!P->hb[i]) CK(cudaMalloc(&P->hb[i], (size_t)n * 16));
+    if (!P->rt) CK(cudaMalloc(&P->rt, n * sizeof(double2)));
+    if (!P->tmp) CK(cudaMalloc(&P->tmp, n * sizeof(double2)));
+    if (!P->tmp2) CK(cudaMalloc(&P->tmp2, n * sizeof(double2)));
+    if (!P->ks.partials) {
+        P->ks.grid = 152 * 4;
+        CK(cudaMalloc(&P->ks.partials, (size_t)P->ks.grid * kChunk * sizeof(double2)));
+    }
+    if (!P->host_scal) CK(cudaMallocHost(&P->host_scal, 8 * sizeof(double)));
+    return MXP_OK;
+}
+
+static mxp_status read_scal(mxp_problem *P, const double *dev, int count)
+{
+    CK(cudaMemcpyAsync(P->host_scal, dev, count * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    return MXP_OK;
+}
+
+// ------------------------------------------------------------------ actions
+
+template <typename S> struct PrecData;
+template <> struct PrecData<double2> {
+    static const double2 *coef(const mxp_problem *P) { return P->coef64; }
+    static const double *kappa(const mxp_problem *P) { return P->kappa64; }
+    static double2 c(cd z) { return make_double2(z.real(), z.imag()); }
+};
+template <> struct PrecData<float2> {
+    static const float2 *coef(const mxp_problem *P) { return P->coef32; }
+    static const float *kappa(const mxp_problem *P) { return P->kappa32; }
+    static float2 c(cd z) { return make_float2((float)z.real(), (float)z.imag()); }
+};
+template <> struct PrecData<__nv_bfloat162> : PrecData<float2> {};
+
+// which = 0: out = exp(i t A_s) x; which = 1: out = psi_1(i t A_s) x.
+// out_mode 1 returns x - result instead (the fixed-point operator of Eq. fixed-point).
+template <typename S>
+static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *out, int out_mode)
+{
+    using C = typename St<S>::C;
+    const TaylorPlan &pl = which ? P->plan_psi : P->plan_exp;
+    S *b[3] = {(S *)P->hb[0], (S *)P->hb[1], (S *)P->hb[2]};
+    S *vs = (S *)P->hb[3];
+    const int64_t n = P->ntot;
+    cudaStream_t st = P->stream;
+    if (which == 0) {
+        launch_convert_in<S>(x, b[0], n, st);
+    } else {
+        launch_convert_in<S>(x, vs, n, st);
+        cudaMemsetAsync(b[0], 0, (size_t)n * sizeof(S), st);
+    }
+    const double t = P->prm.t;
+    const int Ssub = pl.S, m = pl.m;
+    const cd rot(0.0, -t * P->mu / Ssub);                 // scalar row of the augmented matrix / S
+    const cd final_rho = std::exp(cd(0.0, t * P->mu));    // e^{i t mu}
+    cd yxi = which ? cd(1.0) : cd(0.0);
+    StepScalars<C> sc;
+    sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
+    sc.mu = (typename St<S>::R)P->mu;
+    int64_t passes = 0;
+    int iy = 0;
+    for (int sub = 0; sub < Ssub; ++sub) {
+        int in = iy;
+        cd pxi = yxi;
+        for (int k = m; k >= 1; --k) {
+            sc.sigma = PrecData<S>::c(cd(0.0, t / ((double)Ssub * k)));
+            sc.gamma = PrecData<S>::c(which ? pxi / ((double)Ssub * k) : cd(0.0));
+            sc.rho = PrecData<S>::c((sub == Ssub - 1 && k == 1) ? final_rho : cd(1.0));
+            const int o = (in == iy) ? (iy + 1) % 3 : 3 - iy - in;
+            launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc, b[in], b[iy],
+                           which ? vs : nullptr, b[o], st);
+            pxi = yxi + rot * pxi / (double)k;
+            in = o;
+            ++passes;
+        }
+        iy = in;
+        yxi = pxi;
+    }
+    launch_convert_out<S>(b[iy], out, x, out_mode, n, st);
+    P->passes += passes;
+    return passes;
+}
+
+static int64_t phi_dispatch(mxp_problem *P, int which, const double2 *x, double2 *out, int out_mode)
+{
+    switch (P->prm.prec) {
+    case MXP_C64: return phi_action<float2>(P, which, x, out, out_mode);
+    case MXP_BF16S: return phi_action<__nv_bfloat162>(P, which, x, out, out_mode);
+    default: return phi_action<double2>(P, which, x, out, out_mode);
+    }
+}
+
+static void apply_op(mxp_problem *P, int shifted, const double2 *x, double2 *y)
+{
+    StepScalars<double2> sc;
+    sc.zfac = make_double2(1.0, shifted ? P->prm.shift_s : 0.0);
+    sc.mu = 0.0;
+    sc.sigma = make_double2(1.0, 0.0);
+    sc.gamma = make_double2(0.0, 0.0);
+    sc.rho = make_double2(1.0, 0.0);
+    launch_step<double2>(P->geom, P->coef64, P->kappa64, sc, x, nullptr, nullptr, y, P->stream);
+    P->passes += 1;
+}
+
+// One Arnoldi step on V[0..j] -> V[j+1] (the new vector is already in V[j+1]):
+// classical Gram-Schmidt applied twice, normalisation and the Givens update.
+static void arnoldi_step(mxp_problem *P, Arnoldi &a, int j)
+{
+    const int64_t n = P->ntot;
+    cudaStream_t st = P->stream;
+    double2 *w = a.V + (size_t)(j + 1) * n;
+    double2 *col = a.hs.H + (size_t)j * (a.R + 1);
+    krylov_mdot(a.V, n, j + 1, w, n, col, 0, P->ks, st);
+    krylov_maxpy(w, a.V, n, j + 1, col, -1.0, n, st);
+    krylov_mdot(a.V, n, j + 1, w, n, a.tmpcol, 0, P->ks, st);
+    krylov_maxpy(w, a.V, n, j + 1, a.tmpcol, -1.0, n, st);
+    krylov_addvec(col, a.tmpcol, j + 1, st);
+    krylov_nrm2sq(w, n, a.hs.scal, P->ks, st);
+    krylov_scale_invnorm(w, w, a.hs.scal, n, st);
+    hess_update(a.hs, j, st);
+}
+
+// Algorithm 1.
+static mxp_status matexpre_apply(mxp_problem *P, const double2 *r, double2 *w, mxp_apply_stats *stats)
+{
+    CKS(ensure_base(P));
+    const int R = P->prm.inner_restart;
+    CKS(ensure_arnoldi(P, P->inner, R, false));
+    Arnoldi &a = P->inner;
+    const int64_t n = P->ntot;
+    cudaStream_t st = P->stream;
+    const int64_t passes0 = P->passes;
+
+    phi_dispatch(P, 1, r, P->rt, 0);                       // r~ = psi_1(i t A_s) r
+    CK(cudaMemsetAsync(w, 0, n * sizeof(double2), st));
+    krylov_nrm2sq(P->rt, n, a.hs.scal, P->ks, st);
+    hess_start(a.hs, st);
+    krylov_scale_invnorm(a.V, P->rt, a.hs.scal, n, st);
+    CK(cudaGetLastError());
+    CKS(read_scal(P, a.hs.scal, 4));
+    const double zeta = P->host_scal[3];
+    if (!std::isfinite(zeta)) return fail(MXP_ENAN, "psi_1(i t A_s) r is not finite");
+    int total = 0;
+    bool converged = (zeta == 0.0);
+    double est = zeta;
+    const double tol = P->prm.fprtol * zeta;
+    const int fixed = P->prm.inner_fixed;
+    const int target = fixed > 0 ? fixed : P->prm.inner_maxit;
+    while (!converged && total < target) {
+        int j = 0;
+        bool stop = false;
+        for (; j < R && total < target; ++j) {
+            // V[j+1] = (I - exp(i t A_s)) V[j]
+            phi_dispatch(P, 0, a.V + (size_t)j * n, a.V + (size_t)(j + 1) * n, 1);
+            arnoldi_step(P, a, j);
+            ++total;
+            CK(cudaGetLastError());
+            CKS(read_scal(P, a.hs.scal, 3));
+            est = P->host_scal[1];
+            if (!std::isfinite(est)) return fail(MXP_ENAN, "inner GMRES residual is not finite");
+            if (P->host_scal[2] != 0.0) { stop = true; converged = true; ++j; break; }
+            if (fixed <= 0 && est <= tol) { stop = true; converged = true; ++j; break; }
+        }
+        hess_backsolve(a.hs, j, st);
+        krylov_maxpy(w, a.V, n, j, a.hs.y, 1.0, n, st);   // w += V y
+        if (stop || total >= target) break;
+        // restart: residual r~ - (I - exp) w
+        phi_dispatch(P, 0, w, P->tmp, 1);
+        krylov_sub(P->tmp, P->rt, P->tmp, n, st);
+        krylov_nrm2sq(P->tmp, n, a.hs.scal, P->ks, st);
+        hess_start(a.hs, st);
+        krylov_scale_invnorm(a.V, P->tmp, a.hs.scal, n, st);
+        CKS(read_scal(P, a.hs.scal, 4));
+        est = P->host_scal[3];
+        if (!std::isfinite(est)) return fail(MXP_ENAN, "inner GMRES residual is not finite");
+        if (fixed <= 0 && est <= tol) converged = true;
+    }
+    CK(cudaGetLastError());
+    if (stats) {
+        stats->inner_iters = total;
+        stats->converged = converged ? 1 : 0;
+        stats->inner_relres = zeta > 0 ? est / zeta : 0.0;
+        stats->stencil_passes = P->passes - passes0;
+        stats->pt_updates = stats->stencil_passes * n;
+    }
+    return MXP_OK;
+}
+
+// Outer FGMRES(restart), right-preconditioned by Algorithm 1 (Sec. 3.4).
+static mxp_status fgmres_solve(mxp_problem *P, const double2 *b, double2 *x, const mxp_solve_opts *o,
+                               mxp_solve_stats *stats)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    CKS(ensure_base(P));
+    const int R = o->restart;
+    CKS(ensure_arnoldi(P, P->outer, R, true));
+    Arnoldi &a = P->outer;
+    const int64_t n = P->ntot;
+    cudaStream_t st = P->stream;
+    const int64_t passes0 = P->passes;
+    double2 *r = P->tmp2;
+
+    krylov_nrm2sq(b, n, a.hs.scal, P->ks, st);
+    CKS(read_scal(P, a.hs.scal, 1));
+    const double bnorm = std::sqrt(P->host_scal[0]);
+    if (!std::isfinite(bnorm)) return fail(MXP_ENAN, "right-hand side is not finite");
+    if (!o->x0_given) {
+        CK(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
+        krylov_copy(r, b, n, st);
+    } else {
+        apply_op(P, 0, x, r);
+        krylov_sub(r, b, r, n, st);
+    }
+    int total = 0, inner_total = 0;
+    bool converged = false;
+    double est = 0, relres = 1.0;
+    mxp_status status = MXP_OK;
+    if (bnorm == 0.0) {
+        CK(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
+        converged = true;
+        relres = 0;
+    }
+    while (!converged) {
+        krylov_nrm2sq(r, n, a.hs.scal, P->ks, st);
+        hess_start(a.hs, st);
+        krylov_scale_invnorm(a.V, r, a.hs.scal, n, st);
+        CKS(read_scal(P, a.hs.scal, 4));
+        const double beta = P->host_scal[3];
+        if (!std::isfinite(beta)) return fail(MXP_ENAN, "outer residual is not finite");
+        relres = beta / bnorm;
+        if (beta <= o->rtol * bnorm) { converged = true; break; }
+        if (total >= o->maxit) { status = MXP_ENOCONV; break; }
+        int j = 0;
+        for (; j < R && total < o->maxit; ++j) {
+            mxp_apply_stats ast{};
+            CKS(matexpre_apply(P, a.V + (size_t)j * n, a.Z + (size_t)j * n, &ast));
+            inner_total += ast.inner_iters;
+            apply_op(P, 0, a.Z + (size_t)j * n, a.V + (size_t)(j + 1) * n);
+            arnoldi_step(P, a, j);
+            ++total;
+            CK(cudaGetLastError());
+            CKS(read_scal(P, a.hs.scal, 3));
+            est = P->host_scal[1];
+            if (!std::isfinite(est)) return fail(MXP_ENAN, "outer FGMRES residual is not finite");
+            if (P->host_scal[2] != 0.0 || est <= o->rtol * bnorm) { ++j; break; }
+        }
+        hess_backsolve(a.hs, j, st);
+        krylov_maxpy(x, a.Z, n, j, a.hs.y, 1.0, n, st);    // x += Z y
+        apply_op(P, 0, x, r);                               // true residual
+        krylov_sub(r, b, r, n, st);
+        krylov_nrm2sq(r, n, a.hs.scal + 4, P->ks, st);
+        CKS(read_scal(P, a.hs.scal + 4, 1));
+        relres = std::sqrt(P->host_scal[0]) / bnorm;
+        if (!std::isfinite(relres)) return fail(MXP_ENAN, "true residual is not finite");
+        if (relres <= o->rtol) { converged = true; break; }
+        if (total >= o->maxit) { status = MXP_ENOCONV; break; }
+    }
+    CK(cudaStreamSynchronize(st));
+    if (stats) {
+        stats->outer_iters = total;
+        stats->inner_iters_total = inner_total;
+        stats->converged = converged ? 1 : 0;
+        stats->true_relres = relres;
+        stats->est_relres = bnorm > 0 ? est / bnorm : 0.0;
+        stats->stencil_passes = P->passes - passes0;
+        stats->pt_updates = stats->stencil_passes * n;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (status == MXP_ENOCONV) return fail(MXP_ENOCONV, "outer FGMRES reached maxit");
+    return MXP_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char *mxp_status_string(mxp_status s)
+{
+    switch (s) {
+    case MXP_OK: return "ok";
+    case MXP_EINVAL: return "invalid argument";
+    case MXP_ENOMEM: return "out of memory";
+    case MXP_ECUDA: return "CUDA error";
+    case MXP_ENOCONV: return "not converged";
+    case MXP_EBREAKDOWN: return "Krylov breakdown";
+    case MXP_ENAN: return "NaN or Inf";
+    case MXP_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *mxp_last_error(void) { return g_last_error.c_str(); }
+
+mxp_status mxp_default_params(const mxp_grid *grid, double c_min, double ppw, mxp_params *p)
+{
+    if (!grid || !p) return fail(MXP_EINVAL, "NULL argument");
+    if (!(grid->h > 0) || !(c_min > 0) || !(ppw > 0)) return fail(MXP_EINVAL, "h, c_min and ppw must be > 0");
+    const double h = grid->h;
+    const double freq = 1.0 / (ppw * h);
+    std::memset(p, 0, sizeof(*p));
+    p->omega = 2.0 * M_PI * c_min / (ppw * h);
+    p->c_pml = 20.0;
+    p->shift_s = 1.0 / freq;
+    p->t = 40.0 * h * h;
+    p->fprtol = 0.08;
+    p->exp_tol = 1e-12;
+    p->inner_restart = 30;
+    p->inner_maxit = 1000;
+    p->inner_fixed = 0;
+    p->prec = MXP_C128;
+    p->theta_max = 0.0;
+    p->fuse_k = 0;
+    return MXP_OK;
+}
+
+mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, void *cuda_stream,
+                      mxp_problem **out)
+{
+    if (!grid || !c_host || !out) return fail(MXP_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (grid->dim != 2 && grid->dim != 3) return fail(MXP_EINVAL, "dim must be 2 or 3");
+    if (grid->npml < 0) return fail(MXP_EINVAL, "npml must be >= 0");
+    if (!(grid->h > 0) || !std::isfinite(grid->h)) return fail(MXP_EINVAL, "h must be finite and > 0");
+    int64_t ntot = 1;
+    int n[3] = {1, 1, 1};
+    for (int d = 0; d < grid->dim; ++d) {
+        if (grid->n_interior[d] < 1) return fail(MXP_EINVAL, "n_interior must be >= 1");
+        const int64_t nd = grid->n_interior[d] + 2 * (int64_t)grid->npml;
+        if (nd > (1 << 20)) return fail(MXP_EINVAL, "axis too long");
+        n[d] = (int)nd;
+        ntot *= nd;
+    }
+    if (ntot > (int64_t)1 << 34) return fail(MXP_EINVAL, "grid too large");
+    double cmin = 1e300, cmax = 0;
+    for (int64_t i = 0; i < ntot; ++i) {
+        const double v = c_host[i];
+        if (!std::isfinite(v) || v <= 0) return fail(MXP_EINVAL, "wave speed must be finite and > 0 everywhere");
+        cmin = std::min(cmin, v);
+        cmax = std::max(cmax, v);
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(MXP_EINVAL, "no such CUDA device");
+    DeviceGuard guard(device);
+    mxp_problem *P = new mxp_problem();
+    P->device = device;
+    P->stream = (cudaStream_t)cuda_stream;
+    P->grid = *grid;
+    P->geom.dim = grid->dim;
+    for (int d = 0; d < 3; ++d) P->geom.n[d] = n[d];
+    P->geom.s1 = n[0];
+    P->geom.s2 = (int64_t)n[0] * n[1];
+    P->geom.ntot = ntot;
+    P->geom.nmax = std::max(n[0], std::max(n[1], n[2]));
+    P->ntot = ntot;
+    P->cmin = cmin;
+    P->cmax = cmax;
+    mxp_default_params(grid, cmin, 10.0, &P->prm);
+    auto bail = [&](mxp_status s) { mxp_destroy(P); return s; };
+    const size_t cnt = (size_t)9 * P->geom.nmax;
+    if (cudaMalloc(&P->c_dev, ntot * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&P->kappa64, ntot * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&P->kappa32, ntot * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&P->coef64, cnt * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&P->coef32, cnt * sizeof(float2)) != cudaSuccess)
+        return bail(fail(MXP_ENOMEM, "device allocation failed"));
+    if (cudaMemcpyAsync(P->c_dev, c_host, ntot * sizeof(double), cudaMemcpyHostToDevice, P->stream) != cudaSuccess)
+        return bail(fail(MXP_ECUDA, "copy of the medium failed"));
+    mxp_status s = upload_coefs(P);
+    if (s != MXP_OK) return bail(s);
+    update_plans(P);
+    *out = P;
+    return MXP_OK;
+}
+
+mxp_status mxp_set_params(mxp_problem *P, const mxp_params *p)
+{
+    if (!P) return fail(MXP_EINVAL, "NULL problem");
+    mxp_params np;
+    if (p) np = *p;
+    else mxp_default_params(&P->grid, P->cmin, 10.0, &np);
+    CKS(validate_params(&np));
+    DeviceGuard guard(P->device);
+    const bool recoef = np.omega != P->prm.omega || np.c_pml != P->prm.c_pml;
+    P->prm = np;
+    if (recoef) CKS(upload_coefs(P));
+    update_plans(P);
+    return MXP_OK;
+}
+
+mxp_status mxp_get_params(const mxp_problem *P, mxp_params *p)
+{
+    if (!P || !p) return fail(MXP_EINVAL, "NULL argument");
+    *p = P->prm;
+    return MXP_OK;
+}
+
+int64_t mxp_num_unknowns(const mxp_problem *P) { return P ? P->ntot : 0; }
+
+mxp_status mxp_apply_operator(mxp_problem *P, int shifted, const void *x_dev, void *y_dev)
+{
+    if (!P || !x_dev || !y_dev) return fail(MXP_EINVAL, "NULL argument");
+    if (x_dev == y_dev) return fail(MXP_EINVAL, "x and y must not alias");
+    DeviceGuard guard(P->device);
+    apply_op(P, shifted ? 1 : 0, (const double2 *)x_dev, (double2 *)y_dev);
+    CK(cudaGetLastError());
+    return MXP_OK;
+}
+
+mxp_status mxp_apply_phi(mxp_problem *P, int which, const void *x_dev, void *y_dev, int64_t *passes_out)
+{
+    if (!P || !x_dev || !y_dev) return fail(MXP_EINVAL, "NULL argument");
+    if (which != 0 && which != 1) return fail(MXP_EINVAL, "which must be 0 (exp) or 1 (psi_1)");
+    DeviceGuard guard(P->device);
+    CKS(ensure_base(P));
+    const int64_t ps = phi_dispatch(P, which, (const double2 *)x_dev, (double2 *)y_dev, 0);
+    CK(cudaGetLastError());
+    if (passes_out) *passes_out = ps;
+    return MXP_OK;
+}
+
+mxp_status mxp_apply_matexpre(mxp_problem *P, const void *r_dev, void *w_dev, mxp_apply_stats *st)
+{
+    if (!P || !r_dev || !w_dev) return fail(MXP_EINVAL, "NULL argument");
+    if (r_dev == w_dev) return fail(MXP_EINVAL, "r and w must not alias");
+    DeviceGuard guard(P->device);
+    return matexpre_apply(P, (const double2 *)r_dev, (double2 *)w_dev, st);
+}
+
+static mxp_status check_opts(const mxp_solve_opts *o)
+{
+    if (!o) return fail(MXP_EINVAL, "NULL options");
+    if (!(o->rtol > 0) || !(o->rtol < 1)) return fail(MXP_EINVAL, "rtol must lie in (0, 1)");
+    if (o->restart < 1 || o->restart > 64) return fail(MXP_EINVAL, "restart must lie in [1, 64]");
+    if (o->maxit < 1) return fail(MXP_EINVAL, "maxit must be >= 1");
+    return MXP_OK;
+}
+
+mxp_status mxp_solve(mxp_problem *P, const void *b_dev, void *x_dev, const mxp_solve_opts *opts,
+                     mxp_solve_stats *st)
+{
+    if (!P || !b_dev || !x_dev) return fail(MXP_EINVAL, "NULL argument");
+    if (b_dev == x_dev) return fail(MXP_EINVAL, "b and x must not alias");
+    CKS(check_opts(opts));
+    DeviceGuard guard(P->device);
+    return fgmres_solve(P, (const double2 *)b_dev, (double2 *)x_dev, opts, st);
+}
+
+mxp_status mxp_solve_host(mxp_problem *P, const void *b_host, void *x_host, const mxp_solve_opts *opts,
+                          mxp_solve_stats *st)
+{
+    if (!P || !b_host || !x_host) return fail(MXP_EINVAL, "NULL argument");
+    CKS(check_opts(opts));
+    DeviceGuard guard(P->device);
+    const size_t bytes = (size_t)P->ntot * sizeof(double2);
+    if (!P->bdev) CK(cudaMalloc(&P->bdev, bytes));
+    if (!P->xdev) CK(cudaMalloc(&P->xdev, bytes));
+    CK(cudaMemcpyAsync(P->bdev, b_host, bytes, cudaMemcpyHostToDevice, P->stream));
+    if (opts->x0_given) CK(cudaMemcpyAsync(P->xdev, x_host, bytes, cudaMemcpyHostToDevice, P->stream));
+    mxp_status s = fgmres_solve(P, P->bdev, P->xdev, opts, st);
+    if (s != MXP_OK && s != MXP_ENOCONV) return s;
+    CK(cudaMemcpyAsync(x_host, P->xdev, bytes, cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    return s;
+}
+
+mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs, const int *prob_of_rhs,
+                           const void *const *b_dev, void *const *x_dev, const mxp_solve_opts *opts,
+                           mxp_solve_stats *per_rhs)
+{
+    if (!probs || nprob < 1 || nrhs < 0 || (nrhs > 0 && (!prob_of_rhs || !b_dev || !x_dev)))
+        return fail(MXP_EINVAL, "invalid batch arguments");
+    CKS(check_opts(opts));
+    for (int r = 0; r < nrhs; ++r)
+        if (prob_of_rhs[r] < 0 || prob_of_rhs[r] >= nprob || !probs[prob_of_rhs[r]] || !b_dev[r] || !x_dev[r])
+            return fail(MXP_EINVAL, "invalid right-hand side entry");
+    mxp_status worst = MXP_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        mxp_solve_stats s{};
+        mxp_status e = mxp_solve(probs[prob_of_rhs[r]], b_dev[r], x_dev[r], opts, &s);
+        if (per_rhs) per_rhs[r] = s;
+        if (e != MXP_OK && e != MXP_ENOCONV) return e;
+        if (e == MXP_ENOCONV) worst = e;
+    }
+    return worst;
+}
+
+void mxp_destroy(mxp_problem *P)
+{
+    if (!P) return;
+    DeviceGuard guard(P->device);
+    cudaStreamSynchronize(P->stream);
+    cudaFree(P->c_dev); cudaFree(P->kappa64); cudaFree(P->kappa32);
+    cudaFree(P->coef64); cudaFree(P->coef32);
+    for (int i = 0; i < 4; ++i) cudaFree(P->hb[i]);
+    cudaFree(P->rt); cudaFree(P->tmp); cudaFree(P->tmp2); cudaFree(P->bdev); cudaFree(P->xdev);
+    cudaFree(P->ks.partials);
+    if (P->host_scal) cudaFreeHost(P->host_scal);
+    free_arnoldi(P->inner);
+    free_arnoldi(P->outer);
+    delete P;
+}
+
+}  // extern "C"

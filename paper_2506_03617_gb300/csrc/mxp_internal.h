@@ -1,0 +1,138 @@
+// Internal declarations shared by the CUDA translation units of libmatexpre.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/matexpre.h"
+
+namespace mxp {
+
+// ---------------------------------------------------------------- complex math
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Storage traits: S is the type held in global memory for one complex value,
+// C the complex type arithmetic happens in, R its real type.
+template <typename S> struct St;
+template <> struct St<double2> {
+    using R = double; using C = double2;
+    static __device__ __forceinline__ C ld(const double2 *p, int64_t i) { return p[i]; }
+    static __device__ __forceinline__ void st(double2 *p, int64_t i, C v) { p[i] = v; }
+    static __device__ __forceinline__ C from64(double2 v) { return v; }
+};
+template <> struct St<float2> {
+    using R = float; using C = float2;
+    static __device__ __forceinline__ C ld(const float2 *p, int64_t i) { return p[i]; }
+    static __device__ __forceinline__ void st(float2 *p, int64_t i, C v) { p[i] = v; }
+    static __device__ __forceinline__ C from64(double2 v) { return make_float2((float)v.x, (float)v.y); }
+};
+template <> struct St<__nv_bfloat162> {
+    using R = float; using C = float2;
+    static __device__ __forceinline__ C ld(const __nv_bfloat162 *p, int64_t i) { return __bfloat1622float2(p[i]); }
+    static __device__ __forceinline__ void st(__nv_bfloat162 *p, int64_t i, C v) { p[i] = __float22bfloat162_rn(v); }
+    static __device__ __forceinline__ C from64(double2 v) { return make_float2((float)v.x, (float)v.y); }
+};
+
+template <typename C> struct CT;
+template <> struct CT<double2> { using R = double; static __host__ __device__ double2 mk(double a, double b) { return make_double2(a, b); } };
+template <> struct CT<float2> { using R = float; static __host__ __device__ float2 mk(float a, float b) { return make_float2(a, b); } };
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+    int dim;
+    int n[3];          // unknowns per axis (1 for unused axes)
+    int64_t s1, s2;    // strides of axes 1 and 2
+    int64_t ntot;
+    int nmax;          // max_d n[d]: row length of the coefficient table
+};
+
+// Scalars of one Taylor-Horner step  out = rho * (y + sigma * (A_s - mu) p + gamma * v)
+template <typename C> struct StepScalars {
+    C zfac;     // 1 + i s (or 1 for the unshifted operator)
+    typename CT<C>::R mu;
+    C sigma;
+    C gamma;
+    C rho;
+};
+
+// ---------------------------------------------------------------- launchers
+// coef: [dim][3][nmax] complex table: row 0 = a b+ / h^2, row 1 = a b- / h^2,
+// row 2 = their sum (a = 1/s at the node, b+- = 1/s at the half nodes).
+template <typename S>
+void launch_step(const Geom &g, const typename St<S>::C *coef, const typename St<S>::R *kappa,
+                 const StepScalars<typename St<S>::C> &sc, const S *pin, const S *y, const S *v,
+                 S *pout, cudaStream_t st);
+
+// Fused pass: K consecutive Horner steps (k = kfirst, kfirst-1, ..., kfirst-K+1)
+// of one sub-step, tiled through shared memory with a K-cell halo.  Only the
+// 2D kernel exists; returns false if this configuration is not supported.
+template <typename S>
+bool launch_fused(const Geom &g, const typename St<S>::C *coef, const typename St<S>::R *kappa,
+                  int K, const StepScalars<typename St<S>::C> *sc, const S *pin, const S *y,
+                  const S *v, S *pout, cudaStream_t st);
+
+template <typename S>
+void launch_convert_in(const double2 *x, S *out, int64_t n, cudaStream_t st);
+// out = x (mode 0) or out = base - x (mode 1), both complex128
+template <typename S>
+void launch_convert_out(const S *x, double2 *out, const double2 *base, int mode, int64_t n,
+                        cudaStream_t st);
+
+// Krylov kernels (complex128, FP64)
+struct KrylovScratch {
+    double2 *partials = nullptr;   // [kGridRed][kChunk] block partial sums
+    int grid = 0;
+};
+constexpr int kChunk = 8;
+// out[i] (+)= sum_p conj(V_i[p]) w[p] for i < nvec; V_i = V + i * ld.
+void krylov_mdot(const double2 *V, int64_t ld, int nvec, const double2 *w, int64_t n,
+                 double2 *out, int accumulate, const KrylovScratch &ks, cudaStream_t st);
+// w += sign * sum_i coef[i] V_i  (coef on the device)
+void krylov_maxpy(double2 *w, const double2 *V, int64_t ld, int nvec, const double2 *coef,
+                  double sign, int64_t n, cudaStream_t st);
+// ||w||^2 into *out_dev (device double), deterministic
+void krylov_nrm2sq(const double2 *w, int64_t n, double *out_dev, const KrylovScratch &ks,
+                   cudaStream_t st);
+// w = x * (1 / sqrt(*nrm2sq_dev)) if that is > 0
+void krylov_scale_invnorm(double2 *w, const double2 *x, const double *nrm2sq_dev, int64_t n,
+                          cudaStream_t st);
+// y = x - A-ish helpers
+void krylov_sub(double2 *out, const double2 *a, const double2 *b, int64_t n, cudaStream_t st);
+void krylov_copy(double2 *out, const double2 *a, int64_t n, cudaStream_t st);
+void krylov_addvec(double2 *a, const double2 *b, int n, cudaStream_t st);
+// kappa = omega^2 / c^2 in double and float
+void compute_kappa(const double *c, double omega, double *k64, float *k32, int64_t n,
+                   cudaStream_t st);
+
+// Hessenberg / Givens state on the device for one Arnoldi process.
+struct HessState {
+    double2 *H;      // (R+1) x R, column-major: H[j*(R+1)+i]
+    double *cs;      // R
+    double2 *sn;     // R
+    double2 *g;      // R+1
+    double2 *y;      // R
+    double *scal;    // [0] = ||w||^2 of the new vector, [1] = residual estimate |g_{j+1}|,
+                     // [2] = breakdown flag, [3] = beta (initial residual norm)
+    int R;
+};
+// After CGS: H[0..j, j] holds the projections; scal[0] holds ||w||^2.
+// Sets H[j+1,j], applies/creates rotations, updates g, writes scal[1].
+void hess_update(const HessState &hs, int j, cudaStream_t st);
+// g = (beta, 0, ...), beta = sqrt(scal[0]); scal[3] = beta.
+void hess_start(const HessState &hs, cudaStream_t st);
+// Solve the j x j upper-triangular system H y = g into hs.y.
+void hess_backsolve(const HessState &hs, int j, cudaStream_t st);
+
+}  // namespace mxp

@@ -1,0 +1,148 @@
+// Stencil kernels: the PML Helmholtz operator and one Taylor-Horner step of the
+// exponential-integrator actions (Def. psi), for complex128, complex64 and
+// bfloat16-storage vectors.
+//
+// Operator (Eq. helmholtz with the stretched Laplacian of Eq. pml-1d-s on each
+// axis, shift of Sec. 3.4), written with the per-axis coefficient table
+//   wp_d[i] = a_d(i) b_d(i+1/2) / h^2,  wm_d[i] = a_d(i) b_d(i-1/2) / h^2,
+//   wc_d[i] = wp_d[i] + wm_d[i]   (a, b = 1/s at nodes and half nodes):
+//   (A_s p)_q = sum_d (wp_d p_{q+e_d} + wm_d p_{q-e_d} - wc_d p_q)
+//               + kappa_q (1 + i s) p_q,          kappa = omega^2 / c^2,
+// with p = 0 outside the grid (Dirichlet).
+#include "mxp_internal.h"
+
+namespace mxp {
+
+template <typename C>
+__device__ __forceinline__ C czero() { return CT<C>::mk(0, 0); }
+
+// out = rho * ( y + sigma * ((A_s - mu) p) + gamma * v )
+// HAS_Y = false drops y; HAS_V = false drops v.
+template <typename S, int DIM, bool HAS_Y, bool HAS_V>
+__global__ void __launch_bounds__(128) k_step(Geom g, const typename St<S>::C *__restrict__ coef,
+                                              const typename St<S>::R *__restrict__ kappa,
+                                              StepScalars<typename St<S>::C> sc,
+                                              const S *__restrict__ pin, const S *__restrict__ y,
+                                              const S *__restrict__ v, S *__restrict__ pout)
+{
+    using C = typename St<S>::C;
+    using R = typename St<S>::R;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.n[0]) return;
+    const int64_t q = i + g.s1 * j + g.s2 * k;
+    const int nm = g.nmax;
+    const C pc = St<S>::ld(pin, q);
+    C acc = czero<C>();
+    C wcs = czero<C>();
+    {
+        const C xp = (i + 1 < g.n[0]) ? St<S>::ld(pin, q + 1) : czero<C>();
+        const C xm = (i > 0) ? St<S>::ld(pin, q - 1) : czero<C>();
+        acc = cadd(acc, cadd(cmul(coef[i], xp), cmul(coef[nm + i], xm)));
+        wcs = cadd(wcs, coef[2 * nm + i]);
+    }
+    if (DIM >= 2) {
+        const C *cf = coef + 3 * nm;
+        const C xp = (j + 1 < g.n[1]) ? St<S>::ld(pin, q + g.s1) : czero<C>();
+        const C xm = (j > 0) ? St<S>::ld(pin, q - g.s1) : czero<C>();
+        acc = cadd(acc, cadd(cmul(cf[j], xp), cmul(cf[nm + j], xm)));
+        wcs = cadd(wcs, cf[2 * nm + j]);
+    }
+    if (DIM >= 3) {
+        const C *cf = coef + 6 * nm;
+        const C xp = (k + 1 < g.n[2]) ? St<S>::ld(pin, q + g.s2) : czero<C>();
+        const C xm = (k > 0) ? St<S>::ld(pin, q - g.s2) : czero<C>();
+        acc = cadd(acc, cadd(cmul(cf[k], xp), cmul(cf[nm + k], xm)));
+        wcs = cadd(wcs, cf[2 * nm + k]);
+    }
+    const R kp = kappa[q];
+    // diagonal: kappa (1 + i s) - mu - sum_d wc_d
+    const C diag = CT<C>::mk(kp * sc.zfac.x - sc.mu - wcs.x, kp * sc.zfac.y - wcs.y);
+    acc = cadd(acc, cmul(diag, pc));
+    C out = cmul(sc.sigma, acc);
+    if (HAS_Y) out = cadd(out, St<S>::ld(y, q));
+    if (HAS_V) out = cadd(out, cmul(sc.gamma, St<S>::ld(v, q)));
+    out = cmul(sc.rho, out);
+    St<S>::st(pout, q, out);
+}
+
+template <typename S, int DIM>
+static void launch_step_dim(const Geom &g, const typename St<S>::C *coef,
+                            const typename St<S>::R *kappa,
+                            const StepScalars<typename St<S>::C> &sc, const S *pin, const S *y,
+                            const S *v, S *pout, cudaStream_t st)
+{
+    dim3 block(128);
+    dim3 grid((g.n[0] + 127) / 128, g.n[1], g.n[2]);
+    if (y && v) k_step<S, DIM, true, true><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout);
+    else if (y) k_step<S, DIM, true, false><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout);
+    else if (v) k_step<S, DIM, false, true><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout);
+    else k_step<S, DIM, false, false><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout);
+}
+
+template <typename S>
+void launch_step(const Geom &g, const typename St<S>::C *coef, const typename St<S>::R *kappa,
+                 const StepScalars<typename St<S>::C> &sc, const S *pin, const S *y, const S *v,
+                 S *pout, cudaStream_t st)
+{
+    if (g.dim == 3) launch_step_dim<S, 3>(g, coef, kappa, sc, pin, y, v, pout, st);
+    else launch_step_dim<S, 2>(g, coef, kappa, sc, pin, y, v, pout, st);
+}
+
+// ---------------------------------------------------------------- conversions
+template <typename S>
+__global__ void k_convert_in(const double2 *__restrict__ x, S *__restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        St<S>::st(out, i, St<S>::from64(x[i]));
+}
+
+template <typename S>
+__global__ void k_convert_out(const S *__restrict__ x, double2 *__restrict__ out,
+                              const double2 *__restrict__ base, int mode, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const auto c = St<S>::ld(x, i);
+        double2 r = make_double2((double)c.x, (double)c.y);
+        if (mode == 1) r = csub(base[i], r);
+        out[i] = r;
+    }
+}
+
+static int stream_grid(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <typename S>
+void launch_convert_in(const double2 *x, S *out, int64_t n, cudaStream_t st)
+{
+    k_convert_in<S><<<stream_grid(n), 256, 0, st>>>(x, out, n);
+}
+
+template <typename S>
+void launch_convert_out(const S *x, double2 *out, const double2 *base, int mode, int64_t n,
+                        cudaStream_t st)
+{
+    k_convert_out<S><<<stream_grid(n), 256, 0, st>>>(x, out, base, mode, n);
+}
+
+#define MXP_INST(S)                                                                          \
+    template void launch_step<S>(const Geom &, const St<S>::C *, const St<S>::R *,           \
+                                 const StepScalars<St<S>::C> &, const S *, const S *,        \
+                                 const S *, S *, cudaStream_t);                              \
+    template void launch_convert_in<S>(const double2 *, S *, int64_t, cudaStream_t);         \
+    template void launch_convert_out<S>(const S *, double2 *, const double2 *, int, int64_t, \
+                                        cudaStream_t);
+MXP_INST(double2)
+MXP_INST(float2)
+MXP_INST(__nv_bfloat162)
+#undef MXP_INST
+
+}  // namespace mxp

@@ -1,0 +1,261 @@
+"""ctypes binding of libmatexpre (C ABI in ``include/matexpre.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Vectors are torch complex128 CUDA tensors (one value per unknown,
+x fastest); torch supplies device memory and the current stream.  There is no
+CPU fallback: if the library cannot be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+MXP_C128, MXP_C64, MXP_BF16S = 0, 1, 2
+PRECISIONS = {"c128": MXP_C128, "c64": MXP_C64, "bf16s": MXP_BF16S}
+STATUS = {0: "MXP_OK", 1: "MXP_EINVAL", 2: "MXP_ENOMEM", 3: "MXP_ECUDA", 4: "MXP_ENOCONV",
+          5: "MXP_EBREAKDOWN", 6: "MXP_ENAN", 7: "MXP_ETIMEOUT"}
+
+
+class MxpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(ct.Structure):
+    _fields_ = [("dim", ct.c_int), ("n_interior", ct.c_int64 * 3), ("npml", ct.c_int),
+                ("h", ct.c_double)]
+
+
+class Params(ct.Structure):
+    _fields_ = [("omega", ct.c_double), ("c_pml", ct.c_double), ("shift_s", ct.c_double),
+                ("t", ct.c_double), ("fprtol", ct.c_double), ("exp_tol", ct.c_double),
+                ("inner_restart", ct.c_int), ("inner_maxit", ct.c_int),
+                ("inner_fixed", ct.c_int), ("prec", ct.c_int), ("theta_max", ct.c_double),
+                ("fuse_k", ct.c_int)]
+
+
+class ApplyStats(ct.Structure):
+    _fields_ = [("inner_iters", ct.c_int), ("converged", ct.c_int),
+                ("inner_relres", ct.c_double), ("stencil_passes", ct.c_int64),
+                ("pt_updates", ct.c_int64)]
+
+
+class SolveOpts(ct.Structure):
+    _fields_ = [("rtol", ct.c_double), ("restart", ct.c_int), ("maxit", ct.c_int),
+                ("x0_given", ct.c_int)]
+
+
+class SolveStats(ct.Structure):
+    _fields_ = [("outer_iters", ct.c_int), ("inner_iters_total", ct.c_int),
+                ("converged", ct.c_int), ("true_relres", ct.c_double),
+                ("est_relres", ct.c_double), ("stencil_passes", ct.c_int64),
+                ("pt_updates", ct.c_int64), ("seconds", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# name -> (restype, argtypes); every symbol declared in include/matexpre.h
+SIGNATURES = {
+    "mxp_create": (ct.c_int, [ct.POINTER(Grid), ct.POINTER(ct.c_double), ct.c_int, ct.c_void_p,
+                              ct.POINTER(ct.c_void_p)]),
+    "mxp_default_params": (ct.c_int, [ct.POINTER(Grid), ct.c_double, ct.c_double,
+                                      ct.POINTER(Params)]),
+    "mxp_set_params": (ct.c_int, [ct.c_void_p, ct.POINTER(Params)]),
+    "mxp_get_params": (ct.c_int, [ct.c_void_p, ct.POINTER(Params)]),
+    "mxp_apply_operator": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]),
+    "mxp_apply_phi": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
+                                 ct.POINTER(ct.c_int64)]),
+    "mxp_apply_matexpre": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                      ct.POINTER(ApplyStats)]),
+    "mxp_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(SolveOpts),
+                             ct.POINTER(SolveStats)]),
+    "mxp_solve_host": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(SolveOpts),
+                                  ct.POINTER(SolveStats)]),
+    "mxp_solve_batch": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.c_int,
+                                   ct.POINTER(ct.c_int), ct.POINTER(ct.c_void_p),
+                                   ct.POINTER(ct.c_void_p), ct.POINTER(SolveOpts),
+                                   ct.POINTER(SolveStats)]),
+    "mxp_num_unknowns": (ct.c_int64, [ct.c_void_p]),
+    "mxp_destroy": (None, [ct.c_void_p]),
+    "mxp_status_string": (ct.c_char_p, [ct.c_int]),
+    "mxp_last_error": (ct.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmatexpre (building it first if absent).  Raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libmatexpre not found at {path}; run build() first")
+            lib = ct.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        msg = load().mxp_last_error()
+        raise MxpError(status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+        raise ValueError("vectors must be contiguous complex128 CUDA tensors")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ct.c_void_p(stream.cuda_stream)
+
+
+class Problem:
+    """A Helmholtz problem on one GPU: grid, medium c(x) and method parameters."""
+
+    def __init__(self, dim, n_interior, npml, c, h=None, device=0, stream=None, params=None):
+        import torch
+        self._lib = load()
+        self.dim = int(dim)
+        ni = [int(v) for v in n_interior]
+        self.n_interior = tuple(ni)
+        self.npml = int(npml)
+        self.h = float(h) if h is not None else 1.0 / max(ni)
+        self.n = tuple(m + 2 * self.npml for m in ni)
+        self.n_total = int(np.prod(self.n))
+        self.device = int(device)
+        g = Grid()
+        g.dim = self.dim
+        for d in range(3):
+            g.n_interior[d] = ni[d] if d < self.dim else 1
+        g.npml = self.npml
+        g.h = self.h
+        self._grid = g
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1))
+        if c.size != self.n_total:
+            raise ValueError(f"medium has {c.size} values, grid has {self.n_total}")
+        self.cmin = float(c.min())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h_out = ct.c_void_p()
+        _check(self._lib.mxp_create(ct.byref(g), c.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                    self.device, _stream_handle(self.stream), ct.byref(h_out)))
+        self._h = h_out
+        if params is not None:
+            self.set_params(**params)
+
+    @classmethod
+    def from_grid(cls, grid, c, params=None, **kw):
+        p = None
+        if params is not None:
+            p = dict(omega=params.omega, shift_s=params.shift, t=params.t, c_pml=params.cpml,
+                     fprtol=params.fprtol)
+        return cls(grid.dim, grid.ni, grid.npml, c, grid.h, params=p, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mxp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- parameters
+    def get_params(self) -> dict:
+        p = Params()
+        _check(self._lib.mxp_get_params(self._h, ct.byref(p)))
+        return {k: getattr(p, k) for k, _ in Params._fields_}
+
+    def set_params(self, **kw):
+        p = Params()
+        _check(self._lib.mxp_get_params(self._h, ct.byref(p)))
+        for k, v in kw.items():
+            if k == "prec" and isinstance(v, str):
+                v = PRECISIONS[v]
+            setattr(p, k, v)
+        _check(self._lib.mxp_set_params(self._h, ct.byref(p)))
+
+    # -- operations (all on the problem's stream)
+    def empty(self):
+        import torch
+        return torch.empty(self.n_total, dtype=torch.complex128, device=f"cuda:{self.device}")
+
+    def apply_operator(self, x, shifted=False, out=None):
+        y = self.empty() if out is None else out
+        _check(self._lib.mxp_apply_operator(self._h, int(bool(shifted)), _ptr(x), _ptr(y)))
+        return y
+
+    def apply_phi(self, which, x, out=None):
+        y = self.empty() if out is None else out
+        ps = ct.c_int64(0)
+        _check(self._lib.mxp_apply_phi(self._h, int(which), _ptr(x), _ptr(y), ct.byref(ps)))
+        return y, int(ps.value)
+
+    def apply_matexpre(self, r, out=None):
+        w = self.empty() if out is None else out
+        st = ApplyStats()
+        _check(self._lib.mxp_apply_matexpre(self._h, _ptr(r), _ptr(w), ct.byref(st)))
+        return w, {k: getattr(st, k) for k, _ in ApplyStats._fields_}
+
+    def solve(self, b, x=None, rtol=1e-6, restart=30, maxit=500, x0_given=False, check=True):
+        xo = self.empty() if x is None else x
+        o = SolveOpts(rtol, restart, maxit, int(bool(x0_given)))
+        st = SolveStats()
+        s = self._lib.mxp_solve(self._h, _ptr(b), _ptr(xo), ct.byref(o), ct.byref(st))
+        if s != 4 or check:
+            _check(s)
+        return xo, st.as_dict()
+
+    def solve_host(self, b_host: np.ndarray, x_host: np.ndarray, rtol=1e-6, restart=30,
+                   maxit=500, x0_given=False):
+        """Solve with host (numpy complex128) buffers through the host entry point."""
+        assert b_host.dtype == np.complex128 and x_host.dtype == np.complex128
+        assert b_host.flags.c_contiguous and x_host.flags.c_contiguous
+        o = SolveOpts(rtol, restart, maxit, int(bool(x0_given)))
+        st = SolveStats()
+        _check(self._lib.mxp_solve_host(self._h, ct.c_void_p(b_host.ctypes.data),
+                                        ct.c_void_p(x_host.ctypes.data), ct.byref(o),
+                                        ct.byref(st)))
+        return st.as_dict()
+
+
+def solve_batch(problems, prob_of_rhs, bs, xs, rtol=1e-6, restart=30, maxit=500):
+    lib = load()
+    nprob, nrhs = len(problems), len(bs)
+    hp = (ct.c_void_p * nprob)(*[p._h for p in problems])
+    po = (ct.c_int * nrhs)(*prob_of_rhs)
+    bp = (ct.c_void_p * nrhs)(*[_ptr(b).value for b in bs])
+    xp = (ct.c_void_p * nrhs)(*[_ptr(x).value for x in xs])
+    o = SolveOpts(rtol, restart, maxit, 0)
+    st = (SolveStats * max(nrhs, 1))()
+    s = lib.mxp_solve_batch(hp, nprob, nrhs, po, bp, xp, ct.byref(o), st)
+    if s not in (0, 4):
+        _check(s)
+    return [st[i].as_dict() for i in range(nrhs)]
