@@ -1,0 +1,427 @@
+#!/usr/bin/env python3
+"""Benchmark of the MatExPre hot path on GB300.
+
+One step = one full solve of the 2D layered workload (1024^2 interior + 32-cell
+PML = 1088^2 unknowns, layered 1.5-4.5 medium times a +-15% Gaussian random
+field, 8 points per slowest wavelength, Gaussian point source at the centre):
+outer FGMRES(30) in complex128 to a true relative residual of 1e-6, with the
+MatExPre apply (Algorithm 1: psi_1 action + inner GMRES on the exp action) in
+the chosen precision (complex64 by default).  Inputs are resident in HBM when
+the timed region starts; L2 is flushed (256 MiB write) before every step.
+
+value = grid-point updates per second of the whole solve: every stencil sweep
+touches every unknown once, pt_updates = sweeps x unknowns, divided by the
+device time of the solves (CUDA events on the solve stream), summed over ranks
+and divided by the slowest rank's time.
+
+--impl reference times the fp64 CPU oracle (the only reference this work has)
+on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MatExPre-apply Gpts/s, HBM % of peak; time to 1e-6 residual vs plain FP64"
+UNIT = "Gpts/s"
+L2_FLUSH_BYTES = 256 << 20
+# algorithmic bytes per unknown of one exp-action Horner sweep: read p, y, kappa; write p
+BYTES_PER_PT = {"c128": 16 + 16 + 8 + 16, "c64": 8 + 8 + 4 + 8, "bf16s": 4 + 4 + 4 + 4}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["c64", "bf16s", "c128"], default="c64")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="timed solves only (no e2e, roofline, 3D, fp64 or CPU legs)")
+    ap.add_argument("--profile-case", choices=["2d", "3d"], default=None,
+                    help="run two exp actions of the 2D (1088^2) or 3D (288^3) workload "
+                         "and exit; a small command for ncu captures")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload():
+    from paper_2506_03617_gb300 import inputs as I
+    grid, c, p = I.config_2d_layered()
+    b = I.rhs_from_source(I.gaussian_source(grid)).ravel()
+    return grid, c, p, b
+
+
+def config_dict(grid, prec, rtol):
+    return {"workload": "2d_layered_1088",
+            "grid": f"{grid.ni[0]}x{grid.ni[1]} interior + {grid.npml}-cell PML = "
+                    f"{grid.n[0]}x{grid.n[1]} unknowns",
+            "medium": "layered 1.5-4.5 x (1 + 0.15 GRF, corr. 20 cells), seeded",
+            "source": "Gaussian sigma=h at centre", "ppw": 8,
+            "method": f"FGMRES(30) fp64, MatExPre apply in {prec}, fprtol 0.08, t=40h^2, s=1/freq",
+            "rtol": rtol, "l2": "flushed (256 MiB write) before every timed step",
+            "parallelism": "one independent solve per GPU (weak scaling)"}
+
+
+# ----------------------------------------------------------------- oracle sample
+
+def oracle_sample(grid, c, p, frac_t=1.0 / 16.0, seed=1):
+    """Time the fp64 CPU oracle's exp action on the full workload grid and medium
+    with the time length reduced to t/16 (so it takes seconds); returns
+    (pt-updates, seconds, threads)."""
+    import oracle
+    from paper_2506_03617_gb300 import inputs as I
+    P = oracle.Problem(grid.dim, grid.ni, grid.npml, c, p.omega, p.shift, p.t * frac_t,
+                       p.cpml, grid.h)
+    x = I.random_complex(grid.n_total, seed)
+    t0 = time.perf_counter()
+    _, spmv = P.phi(0, x)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return spmv * grid.n_total, dt, threads
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    import oracle
+    oracle.build()
+    grid, c, p, _ = workload()
+    for _ in range(args.warmup):
+        oracle_sample(grid, c, p)
+    pts, secs, threads = 0, 0.0, 1
+    for _ in range(args.steps):
+        a, b, threads = oracle_sample(grid, c, p)
+        pts += a
+        secs += b
+    value = pts / secs / 1e9
+    sample = ("fp64 C oracle exp(i t' A_s) v, t' = t/16, on the full 1088^2 layered grid "
+              "(OpenMP); pt-updates = operator applications x unknowns")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": config_dict(grid, "fp64 (oracle)", 1e-6),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- ours
+
+def kernel_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2506_03617_gb300", "csrc", "stencil.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel, prec):
+    """dram bytes per launch from a committed ncu capture, if taken on the
+    current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        e = rec.get(f"{kernel}:{prec}")
+        if e and e.get("kernel_sha") == kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.cuda.current_device()
+    from paper_2506_03617_gb300 import native as N
+
+    grid, c, p, b_host = workload()
+    n = grid.n_total
+    prob = N.Problem.from_grid(grid, c, p, device=dev)
+    prob.set_params(prec=args.prec, exp_tol=1e-12 if args.prec == "c128" else 1e-6)
+    stream = prob.stream
+    b = torch.from_numpy(b_host).to(f"cuda:{dev}")
+    x = prob.empty()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    rtol = 1e-6
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        prob.solve(b, x, rtol=rtol, maxit=300)
+    barrier()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    launches0 = N.kernel_launch_count()
+    times, pts, stats = [], 0, []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            _, st = prob.solve(b, x, rtol=rtol, maxit=300)
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+            pts += st["pt_updates"]
+            stats.append(st)
+    barrier()
+    launches = N.kernel_launch_count() - launches0
+    clocks = sampler.stop()
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total, float(pts)], dtype=torch.float64, device=f"cuda:{dev}")
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_max, pts_all = float(tmax[0]), float(t[1])
+    else:
+        total_max, pts_all = total, float(pts)
+    value = pts_all / total_max / 1e9
+
+    if args.solve_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "ms_per_step": 1e3 * total_max / args.steps,
+                              "gpu_launches": int(launches), "clocks": clocks,
+                              "partial": "solve-only run"}), flush=True)
+        return 0
+
+    # ---- end to end: host buffers through mxp_solve_host (copies inside the timing)
+    b_pin = torch.from_numpy(b_host).pin_memory().numpy()
+    x_pin = torch.empty(n, dtype=torch.complex128).pin_memory().numpy()
+    e2e_steps = max(1, min(args.steps, 3))
+    e_pts, e_t = 0, 0.0
+    for _ in range(e2e_steps):
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = prob.solve_host(b_pin, x_pin, rtol=rtol, maxit=300)
+        e_t += time.perf_counter() - t0
+        e_pts += st["pt_updates"]
+    e2e = {"value": e_pts / e_t / 1e9 * world, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+           "d2h_bytes_per_step": 16 * n,
+           "note": "mxp_solve_host: pinned host b -> device, solve, device x -> pinned host"}
+
+    # ---- roofline of the dominant kernel (Taylor-Horner sweep of the exp action)
+    xr = torch.from_numpy(np.random.default_rng(3).standard_normal(n) + 0j).to(f"cuda:{dev}")
+    yr = prob.empty()
+    with torch.cuda.stream(stream):
+        prob.apply_phi(0, xr, out=yr)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        reps, passes = 3, 0
+        ev0.record(stream)
+        for _ in range(reps):
+            passes += prob.apply_phi(0, xr, out=yr)[1]
+        ev1.record(stream)
+        ev1.synchronize()
+    sweep_s = ev0.elapsed_time(ev1) / 1e3 / passes
+    peak, peak_kind = measured_peak()
+    bytes_launch = BYTES_PER_PT[args.prec] * n
+    achieved = bytes_launch / sweep_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic("horner_step", args.prec),
+                "kernel": f"k_step<{args.prec}> (one Taylor-Horner sweep of the exp action)",
+                "bytes_per_launch": bytes_launch, "launch_us": sweep_s * 1e6,
+                "peak_kind": f"{peak_kind} (copy bandwidth)",
+                "note": "1088^2 vectors are L2-resident (129 MB L2); the 3D 288^3 line "
+                        "below is the HBM-resident case"}
+
+    extra = {}
+    if world == 1 and rank == 0:
+        # HBM-resident case: 3D 288^3 exp action sweep throughput
+        from paper_2506_03617_gb300 import inputs as I
+        g3, c3, p3 = I.config_3d_homogeneous()
+        del flush
+        P3 = N.Problem.from_grid(g3, c3, p3, device=dev)
+        P3.set_params(prec=args.prec, exp_tol=1e-12 if args.prec == "c128" else 1e-6)
+        x3 = torch.ones(g3.n_total, dtype=torch.complex128, device=f"cuda:{dev}")
+        y3 = P3.empty()
+        with torch.cuda.stream(P3.stream):
+            P3.apply_phi(0, x3, out=y3)
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(P3.stream)
+            ps3 = P3.apply_phi(0, x3, out=y3)[1]
+            ev1.record(P3.stream)
+            ev1.synchronize()
+        t3 = ev0.elapsed_time(ev1) / 1e3
+        sw3 = t3 / ps3
+        a3 = BYTES_PER_PT[args.prec] * g3.n_total / sw3 / 1e9
+        extra["hbm_resident_3d"] = {
+            "workload": "3d_homogeneous_288 (256^3 + 16-cell PML), one exp action",
+            "gpts": g3.n_total * ps3 / t3 / 1e9, "sweeps": ps3, "achieved_gbs": a3,
+            "frac": a3 / peak}
+        del P3, x3, y3
+        torch.cuda.empty_cache()
+        if not args.no_fp64_compare and args.prec != "c128":
+            prob.set_params(prec="c128", exp_tol=1e-12)
+            t0 = time.perf_counter()
+            _, st64 = prob.solve(b, x, rtol=rtol, maxit=300)
+            extra["fp64_solve"] = {"seconds": time.perf_counter() - t0,
+                                   "outer": st64["outer_iters"],
+                                   "inner": st64["inner_iters_total"],
+                                   "true_relres": st64["true_relres"]}
+            prob.set_params(prec=args.prec, exp_tol=1e-6)
+
+    cpu = None
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+        import oracle
+        oracle.build()
+        cp, cs, ct_ = oracle_sample(grid, c, p)
+        cpu = {"value": cp / cs / 1e9, "unit": UNIT, "cores": ct_, "kind": "oracle",
+               "sample": "fp64 C oracle exp(i t' A_s) v with t' = t/16 on the full 1088^2 "
+                         f"layered grid, {cs:.1f} s"}
+
+    if rank == 0:
+        st0 = stats[0]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+                "data": "synthetic", "config": config_dict(grid, args.prec, rtol),
+                "time_to_1e-6_s": total_max / args.steps,
+                "solve": {"outer": st0["outer_iters"], "inner_total": st0["inner_iters_total"],
+                          "true_relres": max(s["true_relres"] for s in stats),
+                          "sweeps": st0["stencil_passes"]},
+                "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+                "gpu_launches": int(launches), "clocks": clocks}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile_case(args):
+    import torch
+    from paper_2506_03617_gb300 import inputs as I
+    from paper_2506_03617_gb300 import native as N
+    if args.profile_case == "3d":
+        g, c, p = I.config_3d_homogeneous()
+    else:
+        g, c, p, _ = workload()
+    prob = N.Problem.from_grid(g, c, p)
+    prob.set_params(prec=args.prec, exp_tol=1e-12 if args.prec == "c128" else 1e-6)
+    x = torch.ones(g.n_total, dtype=torch.complex128, device="cuda")
+    y = prob.empty()
+    for _ in range(2):
+        prob.apply_phi(0, x, out=y)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "prec": args.prec,
+                      "unknowns": g.n_total}))
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

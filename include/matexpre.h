@@ -184,6 +184,10 @@ mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs,
 /* Number of unknowns prod_d n_d of the problem. */
 int64_t mxp_num_unknowns(const mxp_problem *prob);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all problems, all devices); for accounting in benchmarks. */
+int64_t mxp_kernel_launch_count(void);
+
 void mxp_destroy(mxp_problem *prob);
 const char *mxp_status_string(mxp_status s);
 const char *mxp_last_error(void);

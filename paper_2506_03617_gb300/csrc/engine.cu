@@ -626,6 +626,8 @@ const char *mxp_status_string(mxp_status s)
 
 const char *mxp_last_error(void) { return g_last_error.c_str(); }
 
+int64_t mxp_kernel_launch_count(void) { return (int64_t)g_launch_count.load(); }
+
 mxp_status mxp_default_params(const mxp_grid *grid, double c_min, double ppw, mxp_params *p)
 {
     if (!grid || !p) return fail(MXP_EINVAL, "NULL argument");

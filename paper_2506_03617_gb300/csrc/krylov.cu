@@ -6,6 +6,8 @@
 
 namespace mxp {
 
+std::atomic<long long> g_launch_count{0};
+
 constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ double2 warp_sum(double2 v)
@@ -73,11 +75,12 @@ void krylov_mdot(const double2 *V, int64_t ld, int nvec, const double2 *w, int64
         const double2 *Vb = V + base * ld;
         switch (nv) {
 #define MXP_CASE(NVV) \
-    case NVV: k_mdot_partial<NVV><<<ks.grid, kRedThreads, 0, st>>>(Vb, ld, w, n, ks.partials); break;
+    case NVV: count_launch(); k_mdot_partial<NVV><<<ks.grid, kRedThreads, 0, st>>>(Vb, ld, w, n, ks.partials); break;
             MXP_CASE(1) MXP_CASE(2) MXP_CASE(3) MXP_CASE(4)
             MXP_CASE(5) MXP_CASE(6) MXP_CASE(7) MXP_CASE(8)
 #undef MXP_CASE
         }
+        count_launch();
         k_reduce_partials<<<nv, 32, 0, st>>>(ks.partials, ks.grid, nv, out + base, accumulate);
     }
 }
@@ -110,6 +113,7 @@ void krylov_maxpy(double2 *w, const double2 *V, int64_t ld, int nvec, const doub
                   double sign, int64_t n, cudaStream_t st)
 {
     if (nvec <= 0) return;
+    count_launch();
     k_maxpy<<<grid_for(n, 256), 256, 0, st>>>(w, V, ld, nvec, coef, sign, n);
 }
 
@@ -143,7 +147,9 @@ __global__ void k_reduce_real(const double2 *__restrict__ partials, int nblocks,
 void krylov_nrm2sq(const double2 *w, int64_t n, double *out_dev, const KrylovScratch &ks,
                    cudaStream_t st)
 {
+    count_launch();
     k_nrm_partial<<<ks.grid, kRedThreads, 0, st>>>(w, n, ks.partials);
+    count_launch();
     k_reduce_real<<<1, 32, 0, st>>>(ks.partials, ks.grid, out_dev);
 }
 
@@ -162,6 +168,7 @@ __global__ void k_scale_invnorm(double2 *__restrict__ w, const double2 *__restri
 void krylov_scale_invnorm(double2 *w, const double2 *x, const double *nrm2sq_dev, int64_t n,
                           cudaStream_t st)
 {
+    count_launch();
     k_scale_invnorm<<<grid_for(n, 256), 256, 0, st>>>(w, x, nrm2sq_dev, n);
 }
 
@@ -174,6 +181,7 @@ __global__ void k_sub(double2 *out, const double2 *a, const double2 *b, int64_t 
 
 void krylov_sub(double2 *out, const double2 *a, const double2 *b, int64_t n, cudaStream_t st)
 {
+    count_launch();
     k_sub<<<grid_for(n, 256), 256, 0, st>>>(out, a, b, n);
 }
 
@@ -227,6 +235,7 @@ __global__ void k_hess_update(double2 *H, double *cs, double2 *sn, double2 *g, d
 
 void hess_update(const HessState &hs, int j, cudaStream_t st)
 {
+    count_launch();
     k_hess_update<<<1, 1, 0, st>>>(hs.H, hs.cs, hs.sn, hs.g, hs.scal, j, hs.R);
 }
 
@@ -242,6 +251,7 @@ __global__ void k_hess_start(double2 *g, double *scal, int R)
 
 void hess_start(const HessState &hs, cudaStream_t st)
 {
+    count_launch();
     k_hess_start<<<1, 1, 0, st>>>(hs.g, hs.scal, hs.R);
 }
 
@@ -262,6 +272,7 @@ __global__ void k_hess_backsolve(const double2 *H, const double2 *g, double2 *y,
 
 void hess_backsolve(const HessState &hs, int j, cudaStream_t st)
 {
+    count_launch();
     k_hess_backsolve<<<1, 1, 0, st>>>(hs.H, hs.g, hs.y, j, hs.R);
 }
 
@@ -273,6 +284,7 @@ __global__ void k_addvec(double2 *a, const double2 *b, int n)
 
 void krylov_addvec(double2 *a, const double2 *b, int n, cudaStream_t st)
 {
+    count_launch();
     k_addvec<<<(n + 63) / 64, 64, 0, st>>>(a, b, n);
 }
 
@@ -290,6 +302,7 @@ __global__ void k_kappa(const double *__restrict__ c, double w2, double *__restr
 void compute_kappa(const double *c, double omega, double *k64, float *k32, int64_t n,
                    cudaStream_t st)
 {
+    count_launch();
     k_kappa<<<grid_for(n, 256), 256, 0, st>>>(c, omega * omega, k64, k32, n);
 }
 

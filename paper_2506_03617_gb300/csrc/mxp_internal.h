@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -10,6 +11,10 @@
 #include "../../include/matexpre.h"
 
 namespace mxp {
+
+// Number of kernels this library has launched (process-wide).
+extern std::atomic<long long> g_launch_count;
+inline void count_launch(int n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- complex math
 __host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }

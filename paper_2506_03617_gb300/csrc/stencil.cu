@@ -75,6 +75,7 @@ static void launch_step_dim(const Geom &g, const typename St<S>::C *coef,
 {
     dim3 block(128);
     dim3 grid((g.n[0] + 127) / 128, g.n[1], g.n[2]);
+    count_launch();
     if (y && v) k_step<S, DIM, true, true><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout);
     else if (y) k_step<S, DIM, true, false><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout);
     else if (v) k_step<S, DIM, false, true><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout);
@@ -123,6 +124,7 @@ static int stream_grid(int64_t n)
 template <typename S>
 void launch_convert_in(const double2 *x, S *out, int64_t n, cudaStream_t st)
 {
+    count_launch();
     k_convert_in<S><<<stream_grid(n), 256, 0, st>>>(x, out, n);
 }
 
@@ -130,6 +132,7 @@ template <typename S>
 void launch_convert_out(const S *x, double2 *out, const double2 *base, int mode, int64_t n,
                         cudaStream_t st)
 {
+    count_launch();
     k_convert_out<S><<<stream_grid(n), 256, 0, st>>>(x, out, base, mode, n);
 }
 

@@ -86,6 +86,7 @@ SIGNATURES = {
                                    ct.POINTER(ct.c_void_p), ct.POINTER(SolveOpts),
                                    ct.POINTER(SolveStats)]),
     "mxp_num_unknowns": (ct.c_int64, [ct.c_void_p]),
+    "mxp_kernel_launch_count": (ct.c_int64, []),
     "mxp_destroy": (None, [ct.c_void_p]),
     "mxp_status_string": (ct.c_char_p, [ct.c_int]),
     "mxp_last_error": (ct.c_char_p, []),
@@ -244,6 +245,10 @@ class Problem:
                                         ct.c_void_p(x_host.ctypes.data), ct.byref(o),
                                         ct.byref(st)))
         return st.as_dict()
+
+
+def kernel_launch_count() -> int:
+    return int(load().mxp_kernel_launch_count())
 
 
 def solve_batch(problems, prob_of_rhs, bs, xs, rtol=1e-6, restart=30, maxit=500):
