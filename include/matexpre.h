@@ -79,13 +79,19 @@ typedef struct {
  *  prec       precision of the exp / psi_1 actions
  *  theta_max  largest sub-step norm ||t A_s'||/S used by the Taylor actions
  *             (0 = default: 6 for MXP_C128, 4 otherwise)
- *  fuse_k     Taylor steps fused per pass by the tiled kernels (0 = automatic) */
+ *  fuse_k     Taylor steps fused per pass by the tiled 2D kernels of the
+ *             low-precision modes: 0 = chosen by the autotuner, 1 = unfused,
+ *             K > 1 = only tile shapes fusing K steps
+ *  tile_cfg   -1 = autotune the tile shape; >= 0 forces that fused tile
+ *             configuration (2D, MXP_C64 / MXP_BF16S only; see
+ *             mxp_num_tile_configs) */
 typedef struct {
     double omega, c_pml, shift_s, t, fprtol, exp_tol;
     int inner_restart, inner_maxit, inner_fixed;
     mxp_precision prec;
     double theta_max;
     int fuse_k;
+    int tile_cfg;
 } mxp_params;
 
 /* Statistics of one MatExPre apply (Algorithm 1). */
@@ -180,6 +186,12 @@ mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs,
                            const int *prob_of_rhs, const void *const *b_dev,
                            void *const *x_dev, const mxp_solve_opts *opts,
                            mxp_solve_stats *per_rhs);
+
+/* Number of fused 2D tile configurations, and the sweep kernel the problem
+ * currently uses: -1 = unfused, else a configuration index whose fused step
+ * count is returned in *fuse_k (nullable). */
+int mxp_num_tile_configs(void);
+int mxp_tile_config(const mxp_problem *prob, int *fuse_k);
 
 /* Number of unknowns prod_d n_d of the problem. */
 int64_t mxp_num_unknowns(const mxp_problem *prob);

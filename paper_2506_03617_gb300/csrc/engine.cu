@@ -20,6 +20,9 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "mxp_internal.h"
@@ -95,7 +98,9 @@ struct mxp_problem {
     std::vector<double2> coef_host;   // [3][3][nmax]
     // shift and plans
     double mu = 0;
+    double nu = 0, nu_aug = 0;
     TaylorPlan plan_exp, plan_psi;
+    int fused_cfg = -1;        // tile configuration of the fused 2D sweeps, -1 = unfused
     // workspace
     void *hb[4] = {nullptr, nullptr, nullptr, nullptr};   // 16 bytes per unknown each
     double2 *rt = nullptr, *tmp = nullptr, *tmp2 = nullptr;
@@ -236,8 +241,21 @@ static TaylorPlan make_plan(double nu, double tol, double theta_max, int kmult)
 
 static int effective_fuse(const mxp_problem *P)
 {
-    if (P->prm.fuse_k > 0) return P->prm.fuse_k;
-    return 1;
+    return P->fused_cfg >= 0 ? fused2d_cfg_k(P->fused_cfg) : 1;
+}
+
+static double theta_of(const mxp_problem *P)
+{
+    double theta = P->prm.theta_max;
+    if (!(theta > 0)) theta = (P->prm.prec == MXP_C128) ? 6.0 : 4.0;
+    return theta;
+}
+
+static void make_plans(mxp_problem *P)
+{
+    const int km = effective_fuse(P);
+    P->plan_exp = make_plan(P->nu, P->prm.exp_tol, theta_of(P), km);
+    P->plan_psi = make_plan(P->nu_aug, P->prm.exp_tol * 0.1, theta_of(P), km);
 }
 
 static void update_plans(mxp_problem *P)
@@ -261,23 +279,36 @@ static void update_plans(mxp_problem *P)
         else { a = x1; x1 = x2; f1 = f2; x2 = a + gr * (b - a); f2 = nu_of_mu(P, T, x2); }
     }
     P->mu = 0.5 * (a + b);
-    const double nu = nu_of_mu(P, T, P->mu);
-    double theta = P->prm.theta_max;
-    if (!(theta > 0)) theta = (P->prm.prec == MXP_C128) ? 6.0 : 4.0;
-    const int km = effective_fuse(P);
-    P->plan_exp = make_plan(nu, P->prm.exp_tol, theta, km);
-    const double nu_aug = std::max(nu, std::abs(P->prm.t * P->mu));
-    P->plan_psi = make_plan(nu_aug, P->prm.exp_tol * 0.1, theta, km);
+    P->nu = nu_of_mu(P, T, P->mu);
+    P->nu_aug = std::max(P->nu, std::abs(P->prm.t * P->mu));
+    make_plans(P);
+}
+
+// Float coefficient table for the complex64 / bf16-storage sweeps.  The shift
+// mu is folded into the diagonal rows (wc_d + mu/dim, formed in double) so that
+// the large, nearly cancelling terms mu and sum_d wc_d never meet in float; the
+// float kernels are then called with mu = 0.
+static mxp_status upload_coef32(mxp_problem *P)
+{
+    const size_t cnt = P->coef_host.size();
+    const int nm = P->geom.nmax;
+    std::vector<float2> c32(cnt);
+    for (size_t i = 0; i < cnt; ++i) {
+        double re = P->coef_host[i].x;
+        const size_t row = i / nm;
+        if (row % 3 == 2 && (int)(row / 3) < P->grid.dim) re += P->mu / P->grid.dim;
+        c32[i] = make_float2((float)re, (float)P->coef_host[i].y);
+    }
+    CK(cudaMemcpyAsync(P->coef32, c32.data(), cnt * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    return MXP_OK;
 }
 
 static mxp_status upload_coefs(mxp_problem *P)
 {
     build_coef_host(P);
     const size_t cnt = P->coef_host.size();
-    std::vector<float2> c32(cnt);
-    for (size_t i = 0; i < cnt; ++i) c32[i] = make_float2((float)P->coef_host[i].x, (float)P->coef_host[i].y);
     CK(cudaMemcpyAsync(P->coef64, P->coef_host.data(), cnt * sizeof(double2), cudaMemcpyHostToDevice, P->stream));
-    CK(cudaMemcpyAsync(P->coef32, c32.data(), cnt * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
     compute_kappa(P->c_dev, P->prm.omega, P->kappa64, P->kappa32, P->ntot, P->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(P->stream));
@@ -298,7 +329,8 @@ static mxp_status validate_params(const mxp_params *p)
     if (p->inner_fixed < 0) return fail(MXP_EINVAL, "inner_fixed must be >= 0");
     if (p->prec != MXP_C128 && p->prec != MXP_C64 && p->prec != MXP_BF16S) return fail(MXP_EINVAL, "unknown precision");
     if (!fin(p->theta_max) || p->theta_max < 0 || p->theta_max > 30) return fail(MXP_EINVAL, "theta_max must lie in [0, 30]");
-    if (p->fuse_k < 0 || p->fuse_k > 16) return fail(MXP_EINVAL, "fuse_k must lie in [0, 16]");
+    if (p->fuse_k < 0 || p->fuse_k > kMaxFuse) return fail(MXP_EINVAL, "fuse_k must lie in [0, 8]");
+    if (p->tile_cfg < -1 || p->tile_cfg >= fused2d_num_cfgs()) return fail(MXP_EINVAL, "tile_cfg out of range");
     return MXP_OK;
 }
 
@@ -367,6 +399,104 @@ template <> struct PrecData<float2> {
 };
 template <> struct PrecData<__nv_bfloat162> : PrecData<float2> {};
 
+template <typename S>
+static bool fused_pass(mxp_problem *P, int cfg, const FusedStep *steps, const S *pin, const S *y,
+                       const S *v, S *pout)
+{
+    return launch_fused2d<S>(cfg, P->geom, P->grid.npml, P->coef32, P->kappa32, steps,
+                             make_float2(1.0f, (float)P->prm.shift_s), 0.0f,
+                             (float)(1.0 / (P->grid.h * P->grid.h)), pin, y, v, pout, P->stream);
+}
+
+struct TuneKey {
+    int dim, n0, n1, n2, prec, fuse_k;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(dim, n0, n1, n2, prec, fuse_k) < std::tie(o.dim, o.n0, o.n1, o.n2, o.prec, o.fuse_k);
+    }
+};
+static std::map<TuneKey, int> g_tuned;
+static std::mutex g_tune_mutex;
+
+// Pick the sweep kernel for a 2D low-precision problem: time a few passes of
+// every fused tile configuration (and the unfused kernel) on this grid and
+// keep the one with the smallest (sweeps per action) x (time per sweep).
+// fuse_k = 1 forces the unfused kernel, fuse_k = K restricts to that K.
+// Results are cached per (grid, precision, fuse_k) for the process.
+template <typename S>
+static mxp_status tune_fused(mxp_problem *P)
+{
+    P->fused_cfg = -1;
+    if (P->grid.dim != 2 || P->prm.prec == MXP_C128 || P->prm.fuse_k == 1) return MXP_OK;
+    if (P->prm.tile_cfg >= 0) { P->fused_cfg = P->prm.tile_cfg; return MXP_OK; }
+    const TuneKey key{P->grid.dim, P->geom.n[0], P->geom.n[1], P->geom.n[2], (int)P->prm.prec, P->prm.fuse_k};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) { P->fused_cfg = it->second; return MXP_OK; }
+    }
+    CKS(ensure_base(P));
+    const int64_t n = P->ntot;
+    S *b0 = (S *)P->hb[0], *b1 = (S *)P->hb[1], *b2 = (S *)P->hb[2];
+    CK(cudaMemsetAsync(b0, 0, (size_t)n * sizeof(S), P->stream));
+    CK(cudaMemsetAsync(b1, 0, (size_t)n * sizeof(S), P->stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = -1;
+    int best_cfg = -1;
+    for (int cfg = -1; cfg < fused2d_num_cfgs(); ++cfg) {
+        const int K = cfg >= 0 ? fused2d_cfg_k(cfg) : 1;
+        if (P->prm.fuse_k > 1 && K != P->prm.fuse_k) continue;
+        FusedStep steps[kMaxFuse];
+        for (int s = 0; s < K; ++s) steps[s] = FusedStep{1e-9, 0, 0, 1, 0, 0};
+        const int passes = std::max(2, 48 / K);
+        float ms = 0;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, P->stream);
+            for (int i = 0; i < passes; ++i) {
+                if (cfg >= 0) {
+                    fused_pass<S>(P, cfg, steps, (i & 1) ? b2 : b1, b0, nullptr, (i & 1) ? b1 : b2);
+                } else {
+                    StepScalars<typename St<S>::C> sc;
+                    sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
+                    sc.mu = 0;
+                    sc.sigma = PrecData<S>::c(cd(0.0, 1e-9));
+                    sc.gamma = PrecData<S>::c(cd(0.0));
+                    sc.rho = PrecData<S>::c(cd(1.0));
+                    launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc,
+                                   (i & 1) ? b2 : b1, b0, nullptr, (i & 1) ? b1 : b2, P->stream);
+                }
+            }
+            cudaEventRecord(e1, P->stream);
+            CK(cudaEventSynchronize(e1));
+            CK(cudaGetLastError());
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        const double per_step = ms / (passes * (double)K);
+        const TaylorPlan pl = make_plan(P->nu, P->prm.exp_tol, theta_of(P), K);
+        const double cost = per_step * pl.S * pl.m;
+        if (best < 0 || cost < best) { best = cost; best_cfg = cfg; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P->fused_cfg = best_cfg;
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    g_tuned[key] = best_cfg;
+    return MXP_OK;
+}
+
+static mxp_status retune(mxp_problem *P)
+{
+    switch (P->prm.prec) {
+    case MXP_C64: CKS(tune_fused<float2>(P)); break;
+    case MXP_BF16S: CKS(tune_fused<__nv_bfloat162>(P)); break;
+    default: P->fused_cfg = -1; break;
+    }
+    make_plans(P);
+    return MXP_OK;
+}
+
 // which = 0: out = exp(i t A_s) x; which = 1: out = psi_1(i t A_s) x.
 // out_mode 1 returns x - result instead (the fixed-point operator of Eq. fixed-point).
 template <typename S>
@@ -391,9 +521,37 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
     cd yxi = which ? cd(1.0) : cd(0.0);
     StepScalars<C> sc;
     sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
-    sc.mu = (typename St<S>::R)P->mu;
+    sc.mu = (sizeof(S) <= 8) ? (typename St<S>::R)0 : (typename St<S>::R)P->mu;  // float tables carry mu
     int64_t passes = 0;
     int iy = 0;
+    const int cfg = (sizeof(S) <= 8) ? P->fused_cfg : -1;
+    const int K = cfg >= 0 ? fused2d_cfg_k(cfg) : 1;
+    if (cfg >= 0 && m % K == 0) {
+        for (int sub = 0; sub < Ssub; ++sub) {
+            int in = iy;
+            cd pxi = yxi;
+            for (int k = m; k >= 1; k -= K) {
+                FusedStep steps[kMaxFuse];
+                for (int s = 0; s < K; ++s) {
+                    const int kk = k - s;
+                    const cd gam = which ? pxi / ((double)Ssub * kk) : cd(0.0);
+                    const bool last = (sub == Ssub - 1 && kk == 1);
+                    steps[s] = FusedStep{t / ((double)Ssub * kk), gam.real(), gam.imag(),
+                                         final_rho.real(), final_rho.imag(), last ? 1 : 0};
+                    pxi = yxi + rot * pxi / (double)kk;
+                }
+                const int o = (in == iy) ? (iy + 1) % 3 : 3 - iy - in;
+                fused_pass<S>(P, cfg, steps, b[in], b[iy], which ? vs : nullptr, b[o]);
+                in = o;
+                passes += K;
+            }
+            iy = in;
+            yxi = pxi;
+        }
+        launch_convert_out<S>(b[iy], out, x, out_mode, n, st);
+        P->passes += passes;
+        return passes;
+    }
     for (int sub = 0; sub < Ssub; ++sub) {
         int in = iy;
         cd pxi = yxi;
@@ -647,6 +805,7 @@ mxp_status mxp_default_params(const mxp_grid *grid, double c_min, double ppw, mx
     p->prec = MXP_C128;
     p->theta_max = 0.0;
     p->fuse_k = 0;
+    p->tile_cfg = -1;
     return MXP_OK;
 }
 
@@ -706,6 +865,9 @@ mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, vo
     mxp_status s = upload_coefs(P);
     if (s != MXP_OK) return bail(s);
     update_plans(P);
+    s = upload_coef32(P);
+    if (s == MXP_OK) s = retune(P);
+    if (s != MXP_OK) return bail(s);
     *out = P;
     return MXP_OK;
 }
@@ -722,7 +884,8 @@ mxp_status mxp_set_params(mxp_problem *P, const mxp_params *p)
     P->prm = np;
     if (recoef) CKS(upload_coefs(P));
     update_plans(P);
-    return MXP_OK;
+    CKS(upload_coef32(P));
+    return retune(P);
 }
 
 mxp_status mxp_get_params(const mxp_problem *P, mxp_params *p)
@@ -733,6 +896,15 @@ mxp_status mxp_get_params(const mxp_problem *P, mxp_params *p)
 }
 
 int64_t mxp_num_unknowns(const mxp_problem *P) { return P ? P->ntot : 0; }
+
+int mxp_num_tile_configs(void) { return fused2d_num_cfgs(); }
+
+int mxp_tile_config(const mxp_problem *P, int *fuse_k)
+{
+    if (!P) return -1;
+    if (fuse_k) *fuse_k = effective_fuse(P);
+    return P->fused_cfg;
+}
 
 mxp_status mxp_apply_operator(mxp_problem *P, int shifted, const void *x_dev, void *y_dev)
 {

@@ -1,0 +1,254 @@
+// Fused 2D Taylor-Horner sweeps: K consecutive steps of one sub-step per launch
+// (temporal blocking).  Step s computes
+//     p <- rho_s ( y + i tau_s (A_s - mu) p + gamma_s v )
+// with the PML operator of Eq. pml-1d-s (per-axis coefficient table) and the
+// complex shift of Sec. 3.4.  Each CTA loads a region of RX x RY unknowns
+// (its output tile plus a K-cell halo on every side) into shared memory, runs
+// the K steps there, and writes back the inner (RX-2K) x (RY-2K) tile, so one
+// pass reads p, y, kappa (and v) and writes p once for K steps.
+//
+// Thread layout: RX lanes along x (coalesced rows), G groups of RT consecutive
+// rows; a thread walks its RT rows keeping the north/centre/south values in
+// registers, so each step costs one shared load down the column plus the two
+// x-neighbours.  y, v and the per-point diagonal live in registers for the
+// whole pass.  Values at region edges are wrong after a step but the error
+// moves in by one cell per step, so after K steps the inner tile is exact.
+// Unknowns outside the grid are forced to zero (Dirichlet) at every step.
+// Tiles whose region avoids the PML use the real interior coefficients 1/h^2.
+#include "mxp_internal.h"
+
+namespace mxp {
+
+struct FusedScalars {
+    float2 zfac;      // 1 + i s
+    float mu;
+    float ih2;        // 1 / h^2 (interior coefficient)
+    float tau[kMaxFuse];
+    float2 gamma[kMaxFuse];
+    float2 rho;       // applied after the last step when rho_on
+    int rho_on;
+};
+
+template <typename S, int K, int RX, int RT, int G, bool HAS_V>
+__global__ void __launch_bounds__(RX *G) k_fused2d(int n0, int n1, int npml, int nmax,
+                                                   const float2 *__restrict__ coef,
+                                                   const float *__restrict__ kappa,
+                                                   const FusedScalars sc,
+                                                   const S *__restrict__ pin,
+                                                   const S *__restrict__ yv_g,
+                                                   const S *__restrict__ v_g,
+                                                   S *__restrict__ pout)
+{
+    constexpr int RY = RT * G;
+    constexpr int PX = RX + 2;                 // padded row (zero column on each side)
+    constexpr int TXO = RX - 2 * K, TYO = RY - 2 * K;
+    extern __shared__ float2 sm[];
+    float2 *buf0 = sm;
+    float2 *buf1 = sm + (RY + 2) * PX;
+    float2 *cy = buf1 + (RY + 2) * PX;         // [RY][2]: wp_y, wm_y of each region row
+
+    const int tx = threadIdx.x % RX;
+    const int grp = threadIdx.x / RX;
+    const int gx0 = blockIdx.x * TXO - K;
+    const int gy0 = blockIdx.y * TYO - K;
+    const int gx = gx0 + tx;
+    const bool inx = (gx >= 0) && (gx < n0);
+    const bool interior = (gx0 >= npml) && (gx0 + RX <= n0 - npml) && (gy0 >= npml) &&
+                          (gy0 + RY <= n1 - npml);
+
+    // zero the padding frame of both buffers
+    for (int i = threadIdx.x; i < 2 * (RY + 2); i += RX * G) {
+        const int b = i / (RY + 2), r = i % (RY + 2);
+        float2 *buf = b ? buf1 : buf0;
+        buf[r * PX] = make_float2(0.f, 0.f);
+        buf[r * PX + RX + 1] = make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < 2 * RX; i += RX * G) {
+        const int b = i / RX, c = i % RX;
+        float2 *buf = b ? buf1 : buf0;
+        buf[c + 1] = make_float2(0.f, 0.f);
+        buf[(RY + 1) * PX + c + 1] = make_float2(0.f, 0.f);
+    }
+    // y-axis coefficients of the region rows
+    for (int r = threadIdx.x; r < RY; r += RX * G) {
+        const int gy = gy0 + r;
+        float2 wp = make_float2(0.f, 0.f), wm = make_float2(0.f, 0.f);
+        if (gy >= 0 && gy < n1) {
+            wp = coef[3 * nmax + gy];
+            wm = coef[4 * nmax + gy];
+        }
+        cy[2 * r] = wp;
+        cy[2 * r + 1] = wm;
+    }
+    float2 wpx = make_float2(0.f, 0.f), wmx = make_float2(0.f, 0.f), wcx = make_float2(0.f, 0.f);
+    if (inx) {
+        wpx = coef[gx];
+        wmx = coef[nmax + gx];
+        wcx = coef[2 * nmax + gx];
+    }
+
+    float2 yr[RT], dr[RT];
+    float2 vr[HAS_V ? RT : 1];
+    unsigned mask = 0u;
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        const int ry = grp * RT + r;
+        const int gy = gy0 + ry;
+        const bool in = inx && (gy >= 0) && (gy < n1);
+        float2 p = make_float2(0.f, 0.f), yy = make_float2(0.f, 0.f);
+        float2 d = make_float2(0.f, 0.f);
+        if (in) {
+            const int64_t q = (int64_t)gy * n0 + gx;
+            p = St<S>::ld(pin, q);
+            yy = St<S>::ld(yv_g, q);
+            const float kp = kappa[q];
+            const float2 wcy = coef[5 * nmax + gy];
+            d = make_float2(kp * sc.zfac.x - sc.mu - wcx.x - wcy.x, kp * sc.zfac.y - wcx.y - wcy.y);
+            if (HAS_V) vr[HAS_V ? r : 0] = St<S>::ld(v_g, q);
+            mask |= 1u << r;
+        } else if (HAS_V) {
+            vr[HAS_V ? r : 0] = make_float2(0.f, 0.f);
+        }
+        buf0[(ry + 1) * PX + tx + 1] = p;
+        yr[r] = yy;
+        dr[r] = d;
+    }
+    __syncthreads();
+
+#pragma unroll 1
+    for (int s = 0; s < K; ++s) {
+        const float2 *src = (s & 1) ? buf1 : buf0;
+        float2 *dst = (s & 1) ? buf0 : buf1;
+        const float tau = sc.tau[s];
+        const float2 gam = sc.gamma[s];
+        const bool last_rho = (s == K - 1) && sc.rho_on;
+        const int r0 = grp * RT;                // first region row of this thread
+        float2 up = src[r0 * PX + tx + 1];
+        float2 cen = src[(r0 + 1) * PX + tx + 1];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            const int ry = r0 + r;
+            const float2 dn = src[(ry + 2) * PX + tx + 1];
+            const float2 e = src[(ry + 1) * PX + tx + 2];
+            const float2 w = src[(ry + 1) * PX + tx];
+            float2 q;
+            if (interior) {
+                q.x = (e.x + w.x + up.x + dn.x) * sc.ih2;
+                q.y = (e.y + w.y + up.y + dn.y) * sc.ih2;
+            } else {
+                const float2 wpy = cy[2 * ry], wmy = cy[2 * ry + 1];
+                q = cadd(cadd(cmul(wpx, e), cmul(wmx, w)), cadd(cmul(wpy, dn), cmul(wmy, up)));
+            }
+            q = cadd(q, cmul(dr[r], cen));
+            float2 o = make_float2(yr[r].x - tau * q.y, yr[r].y + tau * q.x);
+            if (HAS_V) o = cadd(o, cmul(gam, vr[HAS_V ? r : 0]));
+            if (last_rho) o = cmul(sc.rho, o);
+            if (!((mask >> r) & 1u)) o = make_float2(0.f, 0.f);
+            dst[(ry + 1) * PX + tx + 1] = o;
+            up = cen;
+            cen = dn;
+        }
+        __syncthreads();
+    }
+
+    const float2 *fin = (K & 1) ? buf1 : buf0;
+    if (tx >= K && tx < RX - K) {
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            const int ry = grp * RT + r;
+            if (ry >= K && ry < RY - K && ((mask >> r) & 1u)) {
+                const int64_t q = (int64_t)(gy0 + ry) * n0 + gx;
+                St<S>::st(pout, q, fin[(ry + 1) * PX + tx + 1]);
+            }
+        }
+    }
+}
+
+struct TileCfg {
+    int K, RX, RT, G;
+};
+
+// Tile configurations the tuner may pick from (index = cfg id).
+static const TileCfg kCfgs[] = {
+    {2, 128, 8, 4}, {4, 128, 8, 4}, {8, 128, 8, 4}, {4, 64, 4, 8},
+    {2, 64, 4, 8},  {8, 128, 12, 4}, {4, 128, 4, 4}, {6, 128, 8, 4},
+};
+constexpr int kNumCfgs = sizeof(kCfgs) / sizeof(kCfgs[0]);
+
+int fused2d_num_cfgs() { return kNumCfgs; }
+int fused2d_cfg_k(int id) { return kCfgs[id].K; }
+
+template <typename S, int K, int RX, int RT, int G, bool HAS_V>
+static void launch_one(int n0, int n1, int npml, int nmax, const float2 *coef, const float *kappa,
+                       const FusedScalars &sc, const S *pin, const S *y, const S *v, S *pout,
+                       cudaStream_t st)
+{
+    constexpr int RY = RT * G;
+    const size_t smem = (size_t)(2 * (RY + 2) * (RX + 2) + 2 * RY) * sizeof(float2);
+    static bool configured = false;   // per template instance
+    if (!configured) {
+        cudaFuncSetAttribute(k_fused2d<S, K, RX, RT, G, HAS_V>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    dim3 grid((n0 + RX - 2 * K - 1) / (RX - 2 * K), (n1 + RY - 2 * K - 1) / (RY - 2 * K));
+    count_launch();
+    k_fused2d<S, K, RX, RT, G, HAS_V><<<grid, RX * G, smem, st>>>(n0, n1, npml, nmax, coef, kappa,
+                                                                 sc, pin, y, v, pout);
+}
+
+template <typename S, int K, int RX, int RT, int G>
+static void launch_v(bool hv, int n0, int n1, int npml, int nmax, const float2 *coef,
+                     const float *kappa, const FusedScalars &sc, const S *pin, const S *y,
+                     const S *v, S *pout, cudaStream_t st)
+{
+    if (hv) launch_one<S, K, RX, RT, G, true>(n0, n1, npml, nmax, coef, kappa, sc, pin, y, v, pout, st);
+    else launch_one<S, K, RX, RT, G, false>(n0, n1, npml, nmax, coef, kappa, sc, pin, y, v, pout, st);
+}
+
+template <typename S>
+bool launch_fused2d(int cfg, const Geom &g, int npml, const float2 *coef, const float *kappa,
+                    const FusedStep *steps, const float2 zfac, float mu, float ih2,
+                    const S *pin, const S *y, const S *v, S *pout, cudaStream_t st)
+{
+    if (g.dim != 2 || cfg < 0 || cfg >= kNumCfgs) return false;
+    FusedScalars sc;
+    sc.zfac = zfac;
+    sc.mu = mu;
+    sc.ih2 = ih2;
+    const int K = kCfgs[cfg].K;
+    sc.rho = make_float2(1.f, 0.f);
+    sc.rho_on = 0;
+    for (int s = 0; s < K; ++s) {
+        sc.tau[s] = (float)steps[s].tau;
+        sc.gamma[s] = make_float2((float)steps[s].gamma_re, (float)steps[s].gamma_im);
+        if (steps[s].rho_on) {
+            sc.rho = make_float2((float)steps[s].rho_re, (float)steps[s].rho_im);
+            sc.rho_on = 1;
+        }
+    }
+    const bool hv = (v != nullptr);
+    const int n0 = g.n[0], n1 = g.n[1], nm = g.nmax;
+    switch (cfg) {
+    case 0: launch_v<S, 2, 128, 8, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 1: launch_v<S, 4, 128, 8, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 2: launch_v<S, 8, 128, 8, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 3: launch_v<S, 4, 64, 4, 8>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 4: launch_v<S, 2, 64, 4, 8>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 5: launch_v<S, 8, 128, 12, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 6: launch_v<S, 4, 128, 4, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 7: launch_v<S, 6, 128, 8, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
+    default: return false;
+    }
+    return true;
+}
+
+template bool launch_fused2d<float2>(int, const Geom &, int, const float2 *, const float *,
+                                     const FusedStep *, const float2, float, float, const float2 *,
+                                     const float2 *, const float2 *, float2 *, cudaStream_t);
+template bool launch_fused2d<__nv_bfloat162>(int, const Geom &, int, const float2 *, const float *,
+                                             const FusedStep *, const float2, float, float,
+                                             const __nv_bfloat162 *, const __nv_bfloat162 *,
+                                             const __nv_bfloat162 *, __nv_bfloat162 *, cudaStream_t);
+
+}  // namespace mxp

@@ -80,13 +80,22 @@ void launch_step(const Geom &g, const typename St<S>::C *coef, const typename St
                  const StepScalars<typename St<S>::C> &sc, const S *pin, const S *y, const S *v,
                  S *pout, cudaStream_t st);
 
-// Fused pass: K consecutive Horner steps (k = kfirst, kfirst-1, ..., kfirst-K+1)
-// of one sub-step, tiled through shared memory with a K-cell halo.  Only the
-// 2D kernel exists; returns false if this configuration is not supported.
+// Fused passes (2D): K consecutive Horner steps of one sub-step per launch,
+// tiled through shared memory with a K-cell halo.  Step s uses
+// sigma = i tau, gamma = (gamma_re, gamma_im) and, when rho_on, multiplies the
+// result by rho.  cfg selects a tile shape (see fused2d.cu); returns false if
+// the configuration is not supported (then the caller uses launch_step).
+constexpr int kMaxFuse = 8;
+struct FusedStep {
+    double tau, gamma_re, gamma_im, rho_re, rho_im;
+    int rho_on;
+};
+int fused2d_num_cfgs();
+int fused2d_cfg_k(int cfg);
 template <typename S>
-bool launch_fused(const Geom &g, const typename St<S>::C *coef, const typename St<S>::R *kappa,
-                  int K, const StepScalars<typename St<S>::C> *sc, const S *pin, const S *y,
-                  const S *v, S *pout, cudaStream_t st);
+bool launch_fused2d(int cfg, const Geom &g, int npml, const float2 *coef, const float *kappa,
+                    const FusedStep *steps, const float2 zfac, float mu, float ih2,
+                    const S *pin, const S *y, const S *v, S *pout, cudaStream_t st);
 
 template <typename S>
 void launch_convert_in(const double2 *x, S *out, int64_t n, cudaStream_t st);
