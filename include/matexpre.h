@@ -84,7 +84,11 @@ typedef struct {
  *             K > 1 = only tile shapes fusing K steps
  *  tile_cfg   -1 = autotune the tile shape; >= 0 forces that fused tile
  *             configuration (2D, MXP_C64 / MXP_BF16S only; see
- *             mxp_num_tile_configs) */
+ *             mxp_num_tile_configs)
+ *  persist_cfg  persistent exp-action kernel (2D, MXP_C64 / MXP_BF16S): one
+ *             cooperative launch per exp action with the grid held on chip;
+ *             -1 = used when the autotuner finds it faster, -2 = never,
+ *             >= 0 = force that configuration when the grid fits the GPU */
 typedef struct {
     double omega, c_pml, shift_s, t, fprtol, exp_tol;
     int inner_restart, inner_maxit, inner_fixed;
@@ -92,6 +96,7 @@ typedef struct {
     double theta_max;
     int fuse_k;
     int tile_cfg;
+    int persist_cfg;
 } mxp_params;
 
 /* Statistics of one MatExPre apply (Algorithm 1). */
@@ -192,6 +197,8 @@ mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs,
  * count is returned in *fuse_k (nullable). */
 int mxp_num_tile_configs(void);
 int mxp_tile_config(const mxp_problem *prob, int *fuse_k);
+/* Persistent exp-action kernel in use (-1 = none) and its tile count. */
+int mxp_persist_config(const mxp_problem *prob, int *ntiles);
 
 /* Number of unknowns prod_d n_d of the problem. */
 int64_t mxp_num_unknowns(const mxp_problem *prob);

@@ -101,6 +101,13 @@ struct mxp_problem {
     double nu = 0, nu_aug = 0;
     TaylorPlan plan_exp, plan_psi;
     int fused_cfg = -1;        // tile configuration of the fused 2D sweeps, -1 = unfused
+    int fused_tyo = 0;         // output-tile height of the fused sweeps (0 = largest)
+    double fused_cost = 1e30;  // estimated ms per exp action with the per-pass kernels
+    int persist_cfg = -1;      // persistent exp-action kernel (2D), -1 = not used
+    int p_txo = 0, p_tyo = 0, p_ntx = 0, p_nty = 0;
+    float *tau_dev = nullptr;  // per-step tau / h^2 of the exp plan (persistent kernel)
+    size_t tau_cap = 0;
+    unsigned *bar = nullptr;   // grid-barrier words of the persistent kernel
     // workspace
     void *hb[4] = {nullptr, nullptr, nullptr, nullptr};   // 16 bytes per unknown each
     double2 *rt = nullptr, *tmp = nullptr, *tmp2 = nullptr;
@@ -244,6 +251,11 @@ static int effective_fuse(const mxp_problem *P)
     return P->fused_cfg >= 0 ? fused2d_cfg_k(P->fused_cfg) : 1;
 }
 
+static int exp_fuse(const mxp_problem *P)
+{
+    return P->persist_cfg >= 0 ? persist2d_cfg_k(P->persist_cfg) : effective_fuse(P);
+}
+
 static double theta_of(const mxp_problem *P)
 {
     double theta = P->prm.theta_max;
@@ -253,9 +265,29 @@ static double theta_of(const mxp_problem *P)
 
 static void make_plans(mxp_problem *P)
 {
-    const int km = effective_fuse(P);
-    P->plan_exp = make_plan(P->nu, P->prm.exp_tol, theta_of(P), km);
-    P->plan_psi = make_plan(P->nu_aug, P->prm.exp_tol * 0.1, theta_of(P), km);
+    P->plan_exp = make_plan(P->nu, P->prm.exp_tol, theta_of(P), exp_fuse(P));
+    P->plan_psi = make_plan(P->nu_aug, P->prm.exp_tol * 0.1, theta_of(P), effective_fuse(P));
+}
+
+// Per-step tau / h^2 of the exp plan for the persistent kernel.
+static mxp_status upload_tau(mxp_problem *P)
+{
+    const TaylorPlan &pl = P->plan_exp;
+    const size_t cnt = (size_t)pl.S * pl.m;
+    std::vector<float> tau(cnt);
+    const double h2 = P->grid.h * P->grid.h;
+    for (int sub = 0; sub < pl.S; ++sub)
+        for (int k = pl.m; k >= 1; --k)
+            tau[(size_t)sub * pl.m + (pl.m - k)] = (float)(P->prm.t / ((double)pl.S * k * h2));
+    if (cnt > P->tau_cap) {
+        cudaFree(P->tau_dev);
+        P->tau_dev = nullptr;
+        CK(cudaMalloc(&P->tau_dev, cnt * sizeof(float)));
+        P->tau_cap = cnt;
+    }
+    CK(cudaMemcpyAsync(P->tau_dev, tau.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    return MXP_OK;
 }
 
 static void update_plans(mxp_problem *P)
@@ -331,6 +363,7 @@ static mxp_status validate_params(const mxp_params *p)
     if (!fin(p->theta_max) || p->theta_max < 0 || p->theta_max > 30) return fail(MXP_EINVAL, "theta_max must lie in [0, 30]");
     if (p->fuse_k < 0 || p->fuse_k > kMaxFuse) return fail(MXP_EINVAL, "fuse_k must lie in [0, 8]");
     if (p->tile_cfg < -1 || p->tile_cfg >= fused2d_num_cfgs()) return fail(MXP_EINVAL, "tile_cfg out of range");
+    if (p->persist_cfg < -2 || p->persist_cfg >= persist2d_num_cfgs()) return fail(MXP_EINVAL, "persist_cfg out of range");
     return MXP_OK;
 }
 
@@ -374,13 +407,25 @@ static mxp_status ensure_base(mxp_problem *P)
         CK(cudaMalloc(&P->ks.partials, (size_t)P->ks.grid * kChunk * sizeof(double2)));
     }
     if (!P->host_scal) CK(cudaMallocHost(&P->host_scal, 8 * sizeof(double)));
+    if (!P->bar) {
+        CK(cudaMalloc(&P->bar, 4 * sizeof(unsigned)));
+        CK(cudaMemsetAsync(P->bar, 0, 4 * sizeof(unsigned), P->stream));
+    }
     return MXP_OK;
 }
 
+// Copy `count` device doubles to host_scal[0..count) and the persistent
+// kernel's barrier error word alongside; one stream synchronisation.
 static mxp_status read_scal(mxp_problem *P, const double *dev, int count)
 {
-    CK(cudaMemcpyAsync(P->host_scal, dev, count * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+    if (count > 0)
+        CK(cudaMemcpyAsync(P->host_scal, dev, count * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+    if (P->bar) CK(cudaMemcpyAsync(&P->host_scal[7], P->bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, P->stream));
     CK(cudaStreamSynchronize(P->stream));
+    if (P->bar && *reinterpret_cast<unsigned *>(&P->host_scal[7]) != 0u) {
+        CK(cudaMemsetAsync(P->bar, 0, 4 * sizeof(unsigned), P->stream));
+        return fail(MXP_ETIMEOUT, "grid barrier of the persistent exp kernel timed out");
+    }
     return MXP_OK;
 }
 
@@ -403,7 +448,7 @@ template <typename S>
 static bool fused_pass(mxp_problem *P, int cfg, const FusedStep *steps, const S *pin, const S *y,
                        const S *v, S *pout)
 {
-    return launch_fused2d<S>(cfg, P->geom, P->grid.npml, P->coef32, P->kappa32, steps,
+    return launch_fused2d<S>(cfg, P->fused_tyo, P->geom, P->grid.npml, P->coef32, P->kappa32, steps,
                              make_float2(1.0f, (float)P->prm.shift_s), 0.0f,
                              (float)(1.0 / (P->grid.h * P->grid.h)), pin, y, v, pout, P->stream);
 }
@@ -415,7 +460,9 @@ struct TuneKey {
         return std::tie(dim, n0, n1, n2, prec, fuse_k) < std::tie(o.dim, o.n0, o.n1, o.n2, o.prec, o.fuse_k);
     }
 };
-static std::map<TuneKey, int> g_tuned;
+static std::map<TuneKey, std::pair<int, int>> g_tuned;
+static std::map<TuneKey, double> g_tuned_cost;
+static std::map<TuneKey, int> g_tuned_persist;
 static std::mutex g_tune_mutex;
 
 // Pick the sweep kernel for a 2D low-precision problem: time a few passes of
@@ -427,73 +474,203 @@ template <typename S>
 static mxp_status tune_fused(mxp_problem *P)
 {
     P->fused_cfg = -1;
+    P->fused_tyo = 0;
+    P->fused_cost = 1e30;
     if (P->grid.dim != 2 || P->prm.prec == MXP_C128 || P->prm.fuse_k == 1) return MXP_OK;
     if (P->prm.tile_cfg >= 0) { P->fused_cfg = P->prm.tile_cfg; return MXP_OK; }
     const TuneKey key{P->grid.dim, P->geom.n[0], P->geom.n[1], P->geom.n[2], (int)P->prm.prec, P->prm.fuse_k};
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) { P->fused_cfg = it->second; return MXP_OK; }
+        if (it != g_tuned.end()) {
+            P->fused_cfg = it->second.first;
+            P->fused_tyo = it->second.second;
+            P->fused_cost = g_tuned_cost[key];
+            return MXP_OK;
+        }
     }
     CKS(ensure_base(P));
     const int64_t n = P->ntot;
     S *b0 = (S *)P->hb[0], *b1 = (S *)P->hb[1], *b2 = (S *)P->hb[2];
     CK(cudaMemsetAsync(b0, 0, (size_t)n * sizeof(S), P->stream));
     CK(cudaMemsetAsync(b1, 0, (size_t)n * sizeof(S), P->stream));
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     double best = -1;
-    int best_cfg = -1;
+    int best_cfg = -1, best_tyo = 0;
     for (int cfg = -1; cfg < fused2d_num_cfgs(); ++cfg) {
         const int K = cfg >= 0 ? fused2d_cfg_k(cfg) : 1;
         if (P->prm.fuse_k > 1 && K != P->prm.fuse_k) continue;
+        // output-tile heights to try: the largest, and heights whose tile count
+        // just fits 1..6 waves of two resident CTAs per SM
+        std::vector<int> tyos{0};
+        if (cfg >= 0) {
+            const int maxt = fused2d_cfg_max_tyo(cfg);
+            const int txo = fused2d_cfg_rx(cfg) - 2 * K;
+            const int ntx = (P->geom.n[0] + txo - 1) / txo;
+            for (int waves = 1; waves <= 6; ++waves) {
+                const int nty = (waves * 2 * nsm) / ntx;
+                if (nty < 1) continue;
+                const int tyo = (P->geom.n[1] + nty - 1) / nty;
+                if (tyo >= 2 && tyo < maxt &&
+                    std::find(tyos.begin(), tyos.end(), tyo) == tyos.end())
+                    tyos.push_back(tyo);
+            }
+        }
         FusedStep steps[kMaxFuse];
         for (int s = 0; s < K; ++s) steps[s] = FusedStep{1e-9, 0, 0, 1, 0, 0};
-        const int passes = std::max(2, 48 / K);
-        float ms = 0;
-        for (int rep = 0; rep < 2; ++rep) {
-            cudaEventRecord(e0, P->stream);
-            for (int i = 0; i < passes; ++i) {
-                if (cfg >= 0) {
-                    fused_pass<S>(P, cfg, steps, (i & 1) ? b2 : b1, b0, nullptr, (i & 1) ? b1 : b2);
-                } else {
-                    StepScalars<typename St<S>::C> sc;
-                    sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
-                    sc.mu = 0;
-                    sc.sigma = PrecData<S>::c(cd(0.0, 1e-9));
-                    sc.gamma = PrecData<S>::c(cd(0.0));
-                    sc.rho = PrecData<S>::c(cd(1.0));
-                    launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc,
-                                   (i & 1) ? b2 : b1, b0, nullptr, (i & 1) ? b1 : b2, P->stream);
-                }
-            }
-            cudaEventRecord(e1, P->stream);
-            CK(cudaEventSynchronize(e1));
-            CK(cudaGetLastError());
-            cudaEventElapsedTime(&ms, e0, e1);
-        }
-        const double per_step = ms / (passes * (double)K);
+        const int passes = std::max(4, 96 / K);
         const TaylorPlan pl = make_plan(P->nu, P->prm.exp_tol, theta_of(P), K);
-        const double cost = per_step * pl.S * pl.m;
-        if (best < 0 || cost < best) { best = cost; best_cfg = cfg; }
+        for (int tyo : tyos) {
+            P->fused_tyo = tyo;
+            float best_ms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, P->stream);
+                for (int i = 0; i < passes; ++i) {
+                    if (cfg >= 0) {
+                        fused_pass<S>(P, cfg, steps, (i & 1) ? b2 : b1, b0, nullptr, (i & 1) ? b1 : b2);
+                    } else {
+                        StepScalars<typename St<S>::C> sc;
+                        sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
+                        sc.mu = 0;
+                        sc.sigma = PrecData<S>::c(cd(0.0, 1e-9));
+                        sc.gamma = PrecData<S>::c(cd(0.0));
+                        sc.rho = PrecData<S>::c(cd(1.0));
+                        launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc,
+                                       (i & 1) ? b2 : b1, b0, nullptr, (i & 1) ? b1 : b2, P->stream);
+                    }
+                }
+                cudaEventRecord(e1, P->stream);
+                CK(cudaEventSynchronize(e1));
+                CK(cudaGetLastError());
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) best_ms = std::min(best_ms, ms);   // rep 0 warms up
+            }
+            const double cost = best_ms / (passes * (double)K) * pl.S * pl.m;
+            if (best < 0 || cost < best) { best = cost; best_cfg = cfg; best_tyo = tyo; }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     P->fused_cfg = best_cfg;
+    P->fused_tyo = best_tyo;
+    P->fused_cost = best;
     std::lock_guard<std::mutex> lk(g_tune_mutex);
-    g_tuned[key] = best_cfg;
+    g_tuned[key] = {best_cfg, best_tyo};
+    g_tuned_cost[key] = best;
+    return MXP_OK;
+}
+
+template <typename S>
+static cudaError_t persist_action(mxp_problem *P, const S *x, S *out)
+{
+    const TaylorPlan &pl = P->plan_exp;
+    const int K = persist2d_cfg_k(P->persist_cfg);
+    const cd rho = std::exp(cd(0.0, P->prm.t * P->mu));
+    return launch_persist2d<S>(P->persist_cfg, P->geom, P->grid.npml, P->coef32, P->kappa32,
+                               make_float2(1.0f, (float)P->prm.shift_s),
+                               (float)(P->grid.h * P->grid.h), P->tau_dev, pl.S * pl.m / K, pl.m / K,
+                               make_float2((float)rho.real(), (float)rho.imag()), P->bar, P->p_txo,
+                               P->p_tyo, P->p_ntx, P->p_nty, x, (S *)P->hb[2], (S *)P->hb[3], out,
+                               P->stream);
+}
+
+// Try the persistent exp-action kernels: time one whole action of each
+// configuration that fits the grid and keep it if it beats `best_cost` (ms
+// per action of the per-pass kernels).
+template <typename S>
+static mxp_status tune_persist(mxp_problem *P, double best_cost)
+{
+    P->persist_cfg = -1;
+    if (P->grid.dim != 2 || P->prm.prec == MXP_C128 || P->prm.persist_cfg == -2) return MXP_OK;
+    const bool forced = P->prm.persist_cfg >= 0;
+    if (!forced && (P->prm.fuse_k == 1 || P->prm.tile_cfg >= 0)) return MXP_OK;
+    CKS(ensure_base(P));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = -1, bt[4] = {0, 0, 0, 0};
+    for (int id = 0; id < persist2d_num_cfgs(); ++id) {
+        if (forced && id != P->prm.persist_cfg) continue;
+        if (!forced && P->prm.fuse_k > 1 && persist2d_cfg_k(id) != P->prm.fuse_k) continue;
+        int txo, tyo, ntx, nty;
+        if (!persist2d_plan<S>(id, P->geom.n[0], P->geom.n[1], P->device, &txo, &tyo, &ntx, &nty)) continue;
+        P->persist_cfg = id;
+        P->p_txo = txo; P->p_tyo = tyo; P->p_ntx = ntx; P->p_nty = nty;
+        make_plans(P);
+        CKS(upload_tau(P));
+        float best_ms = 1e30f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            cudaEventRecord(e0, P->stream);
+            if (persist_action<S>(P, (const S *)P->hb[0], (S *)P->hb[1]) != cudaSuccess) { ok = false; cudaGetLastError(); break; }
+            cudaEventRecord(e1, P->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { ok = false; break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best_ms = std::min(best_ms, ms);
+        }
+        CKS(read_scal(P, nullptr, 0));   // barrier error check
+        if (ok && (forced || best_ms < best_cost)) {
+            best_cost = best_ms;
+            best = id;
+            bt[0] = txo; bt[1] = tyo; bt[2] = ntx; bt[3] = nty;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P->persist_cfg = best;
+    P->p_txo = bt[0]; P->p_tyo = bt[1]; P->p_ntx = bt[2]; P->p_nty = bt[3];
+    make_plans(P);
+    if (best >= 0) CKS(upload_tau(P));
+    return MXP_OK;
+}
+
+template <typename S>
+static mxp_status retune_t(mxp_problem *P)
+{
+    CKS(tune_fused<S>(P));
+    make_plans(P);
+    const TuneKey key{P->grid.dim, P->geom.n[0], P->geom.n[1], P->geom.n[2], (int)P->prm.prec,
+                      P->prm.fuse_k * 1000 + P->prm.tile_cfg * 10 + P->prm.persist_cfg};
+    int cached = -3;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tuned_persist.find(key);
+        if (it != g_tuned_persist.end()) cached = it->second;
+    }
+    if (cached == -3) {
+        CKS(tune_persist<S>(P, P->fused_cost));
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tuned_persist[key] = P->persist_cfg;
+    } else if (cached >= 0) {
+        int txo, tyo, ntx, nty;
+        if (persist2d_plan<S>(cached, P->geom.n[0], P->geom.n[1], P->device, &txo, &tyo, &ntx, &nty)) {
+            P->persist_cfg = cached;
+            P->p_txo = txo; P->p_tyo = tyo; P->p_ntx = ntx; P->p_nty = nty;
+            make_plans(P);
+            CKS(upload_tau(P));
+        }
+    } else {
+        P->persist_cfg = -1;
+    }
     return MXP_OK;
 }
 
 static mxp_status retune(mxp_problem *P)
 {
+    P->persist_cfg = -1;
     switch (P->prm.prec) {
-    case MXP_C64: CKS(tune_fused<float2>(P)); break;
-    case MXP_BF16S: CKS(tune_fused<__nv_bfloat162>(P)); break;
+    case MXP_C64: CKS(retune_t<float2>(P)); break;
+    case MXP_BF16S: CKS(retune_t<__nv_bfloat162>(P)); break;
     default: P->fused_cfg = -1; break;
     }
     make_plans(P);
+    if (P->persist_cfg >= 0) CKS(upload_tau(P));
     return MXP_OK;
 }
 
@@ -524,6 +701,16 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
     sc.mu = (sizeof(S) <= 8) ? (typename St<S>::R)0 : (typename St<S>::R)P->mu;  // float tables carry mu
     int64_t passes = 0;
     int iy = 0;
+    if (which == 0 && P->persist_cfg >= 0 && sizeof(S) <= 8) {
+        const cudaError_t ce = persist_action<S>(P, b[0], b[1]);
+        if (ce != cudaSuccess) {
+            fail(MXP_ECUDA, std::string("persistent exp kernel: ") + cudaGetErrorString(ce));
+            return -1;
+        }
+        launch_convert_out<S>(b[1], out, x, out_mode, n, st);
+        P->passes += (int64_t)Ssub * m;
+        return (int64_t)Ssub * m;
+    }
     const int cfg = (sizeof(S) <= 8) ? P->fused_cfg : -1;
     const int K = cfg >= 0 ? fused2d_cfg_k(cfg) : 1;
     if (cfg >= 0 && m % K == 0) {
@@ -624,7 +811,7 @@ static mxp_status matexpre_apply(mxp_problem *P, const double2 *r, double2 *w, m
     cudaStream_t st = P->stream;
     const int64_t passes0 = P->passes;
 
-    phi_dispatch(P, 1, r, P->rt, 0);                       // r~ = psi_1(i t A_s) r
+    if (phi_dispatch(P, 1, r, P->rt, 0) < 0) return MXP_ECUDA;   // r~ = psi_1(i t A_s) r
     CK(cudaMemsetAsync(w, 0, n * sizeof(double2), st));
     krylov_nrm2sq(P->rt, n, a.hs.scal, P->ks, st);
     hess_start(a.hs, st);
@@ -644,7 +831,7 @@ static mxp_status matexpre_apply(mxp_problem *P, const double2 *r, double2 *w, m
         bool stop = false;
         for (; j < R && total < target; ++j) {
             // V[j+1] = (I - exp(i t A_s)) V[j]
-            phi_dispatch(P, 0, a.V + (size_t)j * n, a.V + (size_t)(j + 1) * n, 1);
+            if (phi_dispatch(P, 0, a.V + (size_t)j * n, a.V + (size_t)(j + 1) * n, 1) < 0) return MXP_ECUDA;
             arnoldi_step(P, a, j);
             ++total;
             CK(cudaGetLastError());
@@ -658,7 +845,7 @@ static mxp_status matexpre_apply(mxp_problem *P, const double2 *r, double2 *w, m
         krylov_maxpy(w, a.V, n, j, a.hs.y, 1.0, n, st);   // w += V y
         if (stop || total >= target) break;
         // restart: residual r~ - (I - exp) w
-        phi_dispatch(P, 0, w, P->tmp, 1);
+        if (phi_dispatch(P, 0, w, P->tmp, 1) < 0) return MXP_ECUDA;
         krylov_sub(P->tmp, P->rt, P->tmp, n, st);
         krylov_nrm2sq(P->tmp, n, a.hs.scal, P->ks, st);
         hess_start(a.hs, st);
@@ -806,6 +993,7 @@ mxp_status mxp_default_params(const mxp_grid *grid, double c_min, double ppw, mx
     p->theta_max = 0.0;
     p->fuse_k = 0;
     p->tile_cfg = -1;
+    p->persist_cfg = -1;
     return MXP_OK;
 }
 
@@ -899,6 +1087,13 @@ int64_t mxp_num_unknowns(const mxp_problem *P) { return P ? P->ntot : 0; }
 
 int mxp_num_tile_configs(void) { return fused2d_num_cfgs(); }
 
+int mxp_persist_config(const mxp_problem *P, int *ntiles)
+{
+    if (!P) return -1;
+    if (ntiles) *ntiles = P->persist_cfg >= 0 ? P->p_ntx * P->p_nty : 0;
+    return P->persist_cfg;
+}
+
 int mxp_tile_config(const mxp_problem *P, int *fuse_k)
 {
     if (!P) return -1;
@@ -923,7 +1118,9 @@ mxp_status mxp_apply_phi(mxp_problem *P, int which, const void *x_dev, void *y_d
     DeviceGuard guard(P->device);
     CKS(ensure_base(P));
     const int64_t ps = phi_dispatch(P, which, (const double2 *)x_dev, (double2 *)y_dev, 0);
+    if (ps < 0) return MXP_ECUDA;
     CK(cudaGetLastError());
+    CKS(read_scal(P, nullptr, 0));   // surfaces a persistent-kernel barrier timeout
     if (passes_out) *passes_out = ps;
     return MXP_OK;
 }
@@ -1004,6 +1201,8 @@ void mxp_destroy(mxp_problem *P)
     for (int i = 0; i < 4; ++i) cudaFree(P->hb[i]);
     cudaFree(P->rt); cudaFree(P->tmp); cudaFree(P->tmp2); cudaFree(P->bdev); cudaFree(P->xdev);
     cudaFree(P->ks.partials);
+    cudaFree(P->tau_dev);
+    cudaFree(P->bar);
     if (P->host_scal) cudaFreeHost(P->host_scal);
     free_arnoldi(P->inner);
     free_arnoldi(P->outer);

@@ -30,7 +30,8 @@ struct FusedScalars {
 };
 
 template <typename S, int K, int RX, int RT, int G, bool HAS_V>
-__global__ void __launch_bounds__(RX *G) k_fused2d(int n0, int n1, int npml, int nmax,
+__global__ void __launch_bounds__(RX *G, (RX * G <= 512 && !HAS_V) ? 2 : 1) k_fused2d(int n0, int n1, int npml, int nmax, int TXO,
+                                                   int TYO,
                                                    const float2 *__restrict__ coef,
                                                    const float *__restrict__ kappa,
                                                    const FusedScalars sc,
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(RX *G) k_fused2d(int n0, int n1, int npml, int
 {
     constexpr int RY = RT * G;
     constexpr int PX = RX + 2;                 // padded row (zero column on each side)
-    constexpr int TXO = RX - 2 * K, TYO = RY - 2 * K;
+    // output tile TXO x TYO (<= RX-2K x RY-2K, chosen at run time); region = tile + K halo
     extern __shared__ float2 sm[];
     float2 *buf0 = sm;
     float2 *buf1 = sm + (RY + 2) * PX;
@@ -53,8 +54,8 @@ __global__ void __launch_bounds__(RX *G) k_fused2d(int n0, int n1, int npml, int
     const int gy0 = blockIdx.y * TYO - K;
     const int gx = gx0 + tx;
     const bool inx = (gx >= 0) && (gx < n0);
-    const bool interior = (gx0 >= npml) && (gx0 + RX <= n0 - npml) && (gy0 >= npml) &&
-                          (gy0 + RY <= n1 - npml);
+    const bool interior = (gx0 >= npml) && (gx0 + TXO + 2 * K <= n0 - npml) && (gy0 >= npml) &&
+                          (gy0 + TYO + 2 * K <= n1 - npml);
 
     // zero the padding frame of both buffers
     for (int i = threadIdx.x; i < 2 * (RY + 2); i += RX * G) {
@@ -89,29 +90,36 @@ __global__ void __launch_bounds__(RX *G) k_fused2d(int n0, int n1, int npml, int
 
     float2 yr[RT], dr[RT];
     float2 vr[HAS_V ? RT : 1];
+    float2 pr[RT];
+    float kr[RT];
+    float2 wcyr[RT];
     unsigned mask = 0u;
+    // issue every global load of this thread first (clamped, always-valid
+    // addresses), then mask: many loads in flight instead of one per row
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        const int gy = gy0 + grp * RT + r;
+        const bool in = inx && (gy >= 0) && (gy < n1);
+        if (in) mask |= 1u << r;
+        const int64_t q = in ? (int64_t)gy * n0 + gx : 0;
+        const int gyc = (gy < 0) ? 0 : ((gy >= n1) ? n1 - 1 : gy);
+        pr[r] = St<S>::ld(pin, q);
+        yr[r] = St<S>::ld(yv_g, q);
+        kr[r] = kappa[q];
+        wcyr[r] = coef[5 * nmax + gyc];
+        if (HAS_V) vr[HAS_V ? r : 0] = St<S>::ld(v_g, q);
+    }
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
         const int ry = grp * RT + r;
-        const int gy = gy0 + ry;
-        const bool in = inx && (gy >= 0) && (gy < n1);
-        float2 p = make_float2(0.f, 0.f), yy = make_float2(0.f, 0.f);
-        float2 d = make_float2(0.f, 0.f);
-        if (in) {
-            const int64_t q = (int64_t)gy * n0 + gx;
-            p = St<S>::ld(pin, q);
-            yy = St<S>::ld(yv_g, q);
-            const float kp = kappa[q];
-            const float2 wcy = coef[5 * nmax + gy];
-            d = make_float2(kp * sc.zfac.x - sc.mu - wcx.x - wcy.x, kp * sc.zfac.y - wcx.y - wcy.y);
-            if (HAS_V) vr[HAS_V ? r : 0] = St<S>::ld(v_g, q);
-            mask |= 1u << r;
-        } else if (HAS_V) {
-            vr[HAS_V ? r : 0] = make_float2(0.f, 0.f);
-        }
-        buf0[(ry + 1) * PX + tx + 1] = p;
-        yr[r] = yy;
-        dr[r] = d;
+        const bool in = (mask >> r) & 1u;
+        const float2 zero = make_float2(0.f, 0.f);
+        buf0[(ry + 1) * PX + tx + 1] = in ? pr[r] : zero;
+        yr[r] = in ? yr[r] : zero;
+        if (HAS_V) vr[HAS_V ? r : 0] = in ? vr[HAS_V ? r : 0] : zero;
+        dr[r] = in ? make_float2(kr[r] * sc.zfac.x - sc.mu - wcx.x - wcyr[r].x,
+                                 kr[r] * sc.zfac.y - wcx.y - wcyr[r].y)
+                   : zero;
     }
     __syncthreads();
 
@@ -152,11 +160,11 @@ __global__ void __launch_bounds__(RX *G) k_fused2d(int n0, int n1, int npml, int
     }
 
     const float2 *fin = (K & 1) ? buf1 : buf0;
-    if (tx >= K && tx < RX - K) {
+    if (tx >= K && tx < K + TXO) {
 #pragma unroll
         for (int r = 0; r < RT; ++r) {
             const int ry = grp * RT + r;
-            if (ry >= K && ry < RY - K && ((mask >> r) & 1u)) {
+            if (ry >= K && ry < K + TYO && ((mask >> r) & 1u)) {
                 const int64_t q = (int64_t)(gy0 + ry) * n0 + gx;
                 St<S>::st(pout, q, fin[(ry + 1) * PX + tx + 1]);
             }
@@ -179,9 +187,9 @@ int fused2d_num_cfgs() { return kNumCfgs; }
 int fused2d_cfg_k(int id) { return kCfgs[id].K; }
 
 template <typename S, int K, int RX, int RT, int G, bool HAS_V>
-static void launch_one(int n0, int n1, int npml, int nmax, const float2 *coef, const float *kappa,
-                       const FusedScalars &sc, const S *pin, const S *y, const S *v, S *pout,
-                       cudaStream_t st)
+static void launch_one(int n0, int n1, int npml, int nmax, int tyo, const float2 *coef,
+                       const float *kappa, const FusedScalars &sc, const S *pin, const S *y,
+                       const S *v, S *pout, cudaStream_t st)
 {
     constexpr int RY = RT * G;
     const size_t smem = (size_t)(2 * (RY + 2) * (RX + 2) + 2 * RY) * sizeof(float2);
@@ -191,23 +199,30 @@ static void launch_one(int n0, int n1, int npml, int nmax, const float2 *coef, c
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
-    dim3 grid((n0 + RX - 2 * K - 1) / (RX - 2 * K), (n1 + RY - 2 * K - 1) / (RY - 2 * K));
+    // balance the x tiles: ceil(n0 / (RX-2K)) tiles of equal width
+    const int ntx = (n0 + RX - 2 * K - 1) / (RX - 2 * K);
+    const int txo = (n0 + ntx - 1) / ntx;
+    if (tyo <= 0 || tyo > RY - 2 * K) tyo = RY - 2 * K;
+    dim3 grid(ntx, (n1 + tyo - 1) / tyo);
     count_launch();
-    k_fused2d<S, K, RX, RT, G, HAS_V><<<grid, RX * G, smem, st>>>(n0, n1, npml, nmax, coef, kappa,
-                                                                 sc, pin, y, v, pout);
+    k_fused2d<S, K, RX, RT, G, HAS_V><<<grid, RX * G, smem, st>>>(n0, n1, npml, nmax, txo, tyo,
+                                                                 coef, kappa, sc, pin, y, v, pout);
 }
 
 template <typename S, int K, int RX, int RT, int G>
-static void launch_v(bool hv, int n0, int n1, int npml, int nmax, const float2 *coef,
+static void launch_v(bool hv, int n0, int n1, int npml, int nmax, int tyo, const float2 *coef,
                      const float *kappa, const FusedScalars &sc, const S *pin, const S *y,
                      const S *v, S *pout, cudaStream_t st)
 {
-    if (hv) launch_one<S, K, RX, RT, G, true>(n0, n1, npml, nmax, coef, kappa, sc, pin, y, v, pout, st);
-    else launch_one<S, K, RX, RT, G, false>(n0, n1, npml, nmax, coef, kappa, sc, pin, y, v, pout, st);
+    if (hv) launch_one<S, K, RX, RT, G, true>(n0, n1, npml, nmax, tyo, coef, kappa, sc, pin, y, v, pout, st);
+    else launch_one<S, K, RX, RT, G, false>(n0, n1, npml, nmax, tyo, coef, kappa, sc, pin, y, v, pout, st);
 }
 
+int fused2d_cfg_rx(int id) { return kCfgs[id].RX; }
+int fused2d_cfg_max_tyo(int id) { return kCfgs[id].RT * kCfgs[id].G - 2 * kCfgs[id].K; }
+
 template <typename S>
-bool launch_fused2d(int cfg, const Geom &g, int npml, const float2 *coef, const float *kappa,
+bool launch_fused2d(int cfg, int tyo, const Geom &g, int npml, const float2 *coef, const float *kappa,
                     const FusedStep *steps, const float2 zfac, float mu, float ih2,
                     const S *pin, const S *y, const S *v, S *pout, cudaStream_t st)
 {
@@ -230,23 +245,23 @@ bool launch_fused2d(int cfg, const Geom &g, int npml, const float2 *coef, const 
     const bool hv = (v != nullptr);
     const int n0 = g.n[0], n1 = g.n[1], nm = g.nmax;
     switch (cfg) {
-    case 0: launch_v<S, 2, 128, 8, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 1: launch_v<S, 4, 128, 8, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 2: launch_v<S, 8, 128, 8, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 3: launch_v<S, 4, 64, 4, 8>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 4: launch_v<S, 2, 64, 4, 8>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 5: launch_v<S, 8, 128, 12, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 6: launch_v<S, 4, 128, 4, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 7: launch_v<S, 6, 128, 8, 4>(hv, n0, n1, npml, nm, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 0: launch_v<S, 2, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 1: launch_v<S, 4, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 2: launch_v<S, 8, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 3: launch_v<S, 4, 64, 4, 8>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 4: launch_v<S, 2, 64, 4, 8>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 5: launch_v<S, 8, 128, 12, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 6: launch_v<S, 4, 128, 4, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 7: launch_v<S, 6, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
     default: return false;
     }
     return true;
 }
 
-template bool launch_fused2d<float2>(int, const Geom &, int, const float2 *, const float *,
+template bool launch_fused2d<float2>(int, int, const Geom &, int, const float2 *, const float *,
                                      const FusedStep *, const float2, float, float, const float2 *,
                                      const float2 *, const float2 *, float2 *, cudaStream_t);
-template bool launch_fused2d<__nv_bfloat162>(int, const Geom &, int, const float2 *, const float *,
+template bool launch_fused2d<__nv_bfloat162>(int, int, const Geom &, int, const float2 *, const float *,
                                              const FusedStep *, const float2, float, float,
                                              const __nv_bfloat162 *, const __nv_bfloat162 *,
                                              const __nv_bfloat162 *, __nv_bfloat162 *, cudaStream_t);

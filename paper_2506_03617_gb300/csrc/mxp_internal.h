@@ -92,10 +92,24 @@ struct FusedStep {
 };
 int fused2d_num_cfgs();
 int fused2d_cfg_k(int cfg);
+int fused2d_cfg_max_tyo(int cfg);
+int fused2d_cfg_rx(int cfg);   // largest output-tile height of the configuration
+// tyo: output-tile height (<= fused2d_cfg_max_tyo; <= 0 selects the largest)
 template <typename S>
-bool launch_fused2d(int cfg, const Geom &g, int npml, const float2 *coef, const float *kappa,
+bool launch_fused2d(int cfg, int tyo, const Geom &g, int npml, const float2 *coef, const float *kappa,
                     const FusedStep *steps, const float2 zfac, float mu, float ih2,
                     const S *pin, const S *y, const S *v, S *pout, cudaStream_t st);
+
+// Persistent exp action (2D, float storage types): see persist2d.cu.
+int persist2d_num_cfgs();
+int persist2d_cfg_k(int cfg);
+template <typename S>
+bool persist2d_plan(int cfg, int n0, int n1, int device, int *txo, int *tyo, int *ntx, int *nty);
+template <typename S>
+cudaError_t launch_persist2d(int cfg, const Geom &g, int npml, const float2 *coef, const float *kappa,
+                             float2 zfac, float h2, const float *tau_dev, int npass,
+                             int pass_per_sub, float2 rho, unsigned *bar, int txo, int tyo,
+                             int ntx, int nty, const S *x, S *ex0, S *ex1, S *out, cudaStream_t st);
 
 template <typename S>
 void launch_convert_in(const double2 *x, S *out, int64_t n, cudaStream_t st);

@@ -1,0 +1,366 @@
+// Persistent 2D exp action: one cooperative launch computes a whole
+// exp(i t A_s) v action (all S sub-steps x m Taylor-Horner steps, Def. psi).
+//
+// Each CTA owns one tile of the grid for the whole action.  The tile plus a
+// K-cell ring lives in shared memory (two ping-pong buffers); y (the sub-step
+// start vector) and kappa stay in registers.  One pass = K Horner steps on
+// the region; afterwards the tile interior is exact, the CTA publishes the
+// K-wide strips along its tile edges to a global exchange buffer, all CTAs meet
+// at a grid barrier, and each CTA refreshes its ring from its neighbours'
+// strips.  Global traffic per pass is only these strips (L2-resident), and
+// there is one launch per action instead of one per pass.
+//
+// The grid barrier spins with a bounded iteration count; on timeout it sets an
+// error flag and every CTA leaves the pass loop, so the kernel always ends.
+// Co-residency of all CTAs is guaranteed by the cooperative launch (the launch
+// fails instead of deadlocking when the grid does not fit).
+#include "mxp_internal.h"
+
+namespace mxp {
+
+struct PersistArgs {
+    int n0, n1, nmax, npml;
+    int txo, tyo, ntx, nty;      // tile extents and tile counts
+    const float2 *coef;
+    const float *kappa;
+    float2 zfac;                 // 1 + i s
+    float h2;                    // h^2: operator scaled to dimensionless units
+    const float *tau;            // per step: tau / h^2 (operator scaled by h^2), npass * K
+    int npass, pass_per_sub;     // passes in total and per sub-step
+    float2 rho;                  // applied at the very last step
+    unsigned *bar;               // [0] arrival count, [1] generation, [2] error flag
+};
+
+constexpr long long kBarrierSpinLimit = 1ll << 24;   // x >= 32 ns sleep: about a second
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        volatile unsigned *verr = bar + 2;
+        int ok = 1;
+        __threadfence();
+        const unsigned gen = *vgen;
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == gen) {
+                if (++it > kBarrierSpinLimit || *verr != 0u) {
+                    atomicExch(bar + 2, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok && (*verr == 0u);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename S, int K, int BX, int BG, int R, int CH>
+__global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S *__restrict__ x,
+                                                         S *__restrict__ ex0,
+                                                         S *__restrict__ ex1,
+                                                         S *__restrict__ out)
+{
+    static_assert(K % 2 == 0, "K must be even: each pass starts and ends in buffer 0");
+    static_assert(R % CH == 0, "rows per thread must be a multiple of the chunk");
+    constexpr int PX = BX + 2;
+    constexpr int PY = BG * R + 2;
+    extern __shared__ float2 sm[];
+    float2 *b0 = sm;
+    float2 *b1 = sm + PY * PX;
+    float2 *cy = b1 + PY * PX;          // [BG*R][3] scaled y-axis coefficients wp, wm, wc of region rows
+    float *ks = reinterpret_cast<float *>(cy + 3 * BG * R);   // [BG*R][BX] kappa of the region
+
+    const int tx = threadIdx.x % BX;
+    const int grp = threadIdx.x / BX;
+    const int bx = blockIdx.x % a.ntx, by = blockIdx.x / a.ntx;
+    const int RW = a.txo + 2 * K, RH = a.tyo + 2 * K;       // region extents
+    const int gx0 = bx * a.txo - K, gy0 = by * a.tyo - K;
+    const int gx = gx0 + tx;
+    const bool colok = (tx < RW);
+    const bool inx = colok && gx >= 0 && gx < a.n0;
+    const int n0 = a.n0, n1 = a.n1, nm = a.nmax;
+    const float h2 = a.h2;
+
+    for (int i = threadIdx.x; i < 2 * PY * PX; i += BX * BG) sm[i] = make_float2(0.f, 0.f);
+    for (int r = threadIdx.x; r < BG * R; r += BX * BG) {
+        const int gy = gy0 + r;
+        float2 wp = make_float2(0.f, 0.f), wm = make_float2(0.f, 0.f), wc = make_float2(0.f, 0.f);
+        if (gy >= 0 && gy < n1) {
+            wp = a.coef[3 * nm + gy];
+            wm = a.coef[4 * nm + gy];
+            wc = a.coef[5 * nm + gy];
+        }
+        cy[3 * r] = make_float2(wp.x * h2, wp.y * h2);
+        cy[3 * r + 1] = make_float2(wm.x * h2, wm.y * h2);
+        cy[3 * r + 2] = make_float2(wc.x * h2, wc.y * h2);
+    }
+    float2 wpx = make_float2(0.f, 0.f), wmx = make_float2(0.f, 0.f), wcx = make_float2(0.f, 0.f);
+    if (inx) {
+        wpx = a.coef[gx];
+        wmx = a.coef[nm + gx];
+        wcx = a.coef[2 * nm + gx];
+    }
+    wpx = make_float2(wpx.x * h2, wpx.y * h2);
+    wmx = make_float2(wmx.x * h2, wmx.y * h2);
+    wcx = make_float2(wcx.x * h2, wcx.y * h2);
+    const float2 zh = make_float2(a.zfac.x * h2, a.zfac.y * h2);
+    __syncthreads();
+
+    // per-point state: y (sub-step start) in registers, kappa in shared memory
+    float2 yr[R];
+    unsigned inmask = 0u;     // point inside the grid and the region
+    unsigned tilemask = 0u;   // point inside this CTA's tile
+    unsigned stripmask = 0u;  // tile point within K of the tile edge (published)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int ry = grp * R + r;
+        const int gy = gy0 + ry;
+        const bool in = inx && ry < RH && gy >= 0 && gy < n1;
+        const int64_t q = in ? (int64_t)gy * n0 + gx : 0;
+        const float2 p0 = St<S>::ld(x, q);
+        ks[ry * BX + tx] = a.kappa[q];
+        yr[r] = in ? p0 : make_float2(0.f, 0.f);
+        if (in) {
+            inmask |= 1u << r;
+            b0[(ry + 1) * PX + tx + 1] = p0;
+            const bool intile = tx >= K && tx < K + a.txo && ry >= K && ry < K + a.tyo;
+            if (intile) {
+                tilemask |= 1u << r;
+                if (tx < 2 * K || tx >= a.txo || ry < 2 * K || ry >= a.tyo) stripmask |= 1u << r;
+            }
+        }
+    }
+    __syncthreads();
+
+    const unsigned nblocks = gridDim.x;
+    bool alive = true;
+    for (int pass = 0; pass < a.npass && alive; ++pass) {
+#pragma unroll 1
+        for (int s = 0; s < K; ++s) {
+            const float2 *src = (s & 1) ? b1 : b0;
+            float2 *dst = (s & 1) ? b0 : b1;
+            const float tau = a.tau[pass * K + s];
+            const bool last = (pass == a.npass - 1) && (s == K - 1);
+            const int r0 = grp * R;
+            float2 up = src[r0 * PX + tx + 1];
+            float2 cen = src[(r0 + 1) * PX + tx + 1];
+            // rows in chunks of CH: all shared loads of a chunk are issued before
+            // any of its stores, so they overlap instead of waiting row by row
+#pragma unroll
+            for (int c = 0; c < R; c += CH) {
+                if (r0 + c >= RH) break;                 // uniform across the warp
+                float2 dn[CH], e[CH], w[CH], o[CH];
+                float kk[CH];
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    const int ry = r0 + c + j;
+                    dn[j] = src[(ry + 2) * PX + tx + 1];
+                    e[j] = src[(ry + 1) * PX + tx + 2];
+                    w[j] = src[(ry + 1) * PX + tx];
+                    kk[j] = ks[ry * BX + tx];
+                }
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    const int ry = r0 + c + j;
+                    const float2 wpy = cy[3 * ry], wmy = cy[3 * ry + 1], wcy = cy[3 * ry + 2];
+                    // scaled diagonal h^2 (kappa (1 + i s) - wc_x - wc_y); mu is folded in wc
+                    const float2 d = make_float2(fmaf(kk[j], zh.x, -(wcx.x + wcy.x)),
+                                                 fmaf(kk[j], zh.y, -(wcx.y + wcy.y)));
+                    float2 q = cadd(cadd(cmul(wpx, e[j]), cmul(wmx, w[j])),
+                                    cadd(cmul(wpy, dn[j]), cmul(wmy, up)));
+                    q = cadd(q, cmul(d, cen));
+                    o[j] = make_float2(yr[c + j].x - tau * q.y, yr[c + j].y + tau * q.x);
+                    if (last) o[j] = cmul(a.rho, o[j]);
+                    up = cen;
+                    cen = dn[j];
+                }
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    const int ry = r0 + c + j;
+                    if ((inmask >> (c + j)) & 1u) dst[(ry + 1) * PX + tx + 1] = o[j];
+                }
+            }
+            __syncthreads();
+        }
+        if (pass == a.npass - 1) break;
+        // publish the tile's edge strips, meet, pull the ring from the neighbours
+        S *ex = (pass & 1) ? ex1 : ex0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if ((stripmask >> r) & 1u) {
+                const int ry = grp * R + r;
+                const int64_t q = (int64_t)(gy0 + ry) * n0 + gx;
+                St<S>::st(ex, q, b0[(ry + 1) * PX + tx + 1]);
+            }
+        }
+        alive = grid_barrier(a.bar, nblocks);
+        if (!alive) break;
+        const bool sub_end = ((pass + 1) % a.pass_per_sub) == 0;
+        // ring refresh: issue every L2 load first (clamped addresses), then store
+        const unsigned ring = inmask & ~tilemask;
+        if (ring) {
+            float2 rv[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int ry = grp * R + r;
+                const int64_t q = ((ring >> r) & 1u) ? (int64_t)(gy0 + ry) * n0 + gx : 0;
+                if (sizeof(S) == 8) {
+                    rv[r] = __ldcg(reinterpret_cast<const float2 *>(ex) + q);
+                } else {
+                    const unsigned u = __ldcg(reinterpret_cast<const unsigned *>(ex) + q);
+                    rv[r] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if ((ring >> r) & 1u) b0[(grp * R + r + 1) * PX + tx + 1] = rv[r];
+        }
+        __syncthreads();
+        if (sub_end) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if ((inmask >> r) & 1u) yr[r] = b0[(grp * R + r + 1) * PX + tx + 1];
+        }
+    }
+    if (alive) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if ((tilemask >> r) & 1u) {
+                const int ry = grp * R + r;
+                St<S>::st(out, (int64_t)(gy0 + ry) * n0 + gx, b0[(ry + 1) * PX + tx + 1]);
+            }
+        }
+    }
+}
+
+struct PCfg {
+    int K, BX, BG, R;
+};
+static const PCfg kPCfgs[] = {{2, 128, 4, 18}, {4, 96, 4, 28}, {4, 128, 4, 20}};
+constexpr int kNumP = sizeof(kPCfgs) / sizeof(kPCfgs[0]);
+
+int persist2d_num_cfgs() { return kNumP; }
+int persist2d_cfg_k(int id) { return kPCfgs[id].K; }
+
+template <typename S, int K, int BX, int BG, int R>
+static void *kernel_ptr() { return (void *)k_persist2d<S, K, BX, BG, R, (R % 4 == 0) ? 4 : 2>; }
+
+template <typename S, int K, int BX, int BG, int R>
+static size_t smem_bytes()
+{
+    return (size_t)(2 * (BG * R + 2) * (BX + 2) + 3 * BG * R) * sizeof(float2) +
+           (size_t)BG * R * BX * sizeof(float);
+}
+
+template <typename S>
+static void cfg_info(int id, void **fn, size_t *smem)
+{
+    switch (id) {
+    case 0: *fn = kernel_ptr<S, 2, 128, 4, 18>(); *smem = smem_bytes<S, 2, 128, 4, 18>(); break;
+    case 1: *fn = kernel_ptr<S, 4, 96, 4, 28>(); *smem = smem_bytes<S, 4, 96, 4, 28>(); break;
+    default: *fn = kernel_ptr<S, 4, 128, 4, 20>(); *smem = smem_bytes<S, 4, 128, 4, 20>(); break;
+    }
+}
+
+// Tile plan for configuration id on an n0 x n1 grid: the largest number of
+// tiles that fits the co-resident CTAs, each no larger than the register /
+// shared-memory region of the configuration.  Returns false if the grid does
+// not fit on this device.
+template <typename S>
+bool persist2d_plan(int id, int n0, int n1, int device, int *txo, int *tyo, int *ntx, int *nty)
+{
+    if (id < 0 || id >= kNumP) return false;
+    void *fn;
+    size_t smem;
+    cfg_info<S>(id, &fn, &smem);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int per_sm = 0, nsm = 0;
+    const PCfg c = kPCfgs[id];
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c.BX * c.BG, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    const int slots = per_sm * nsm;
+    const int txmax = c.BX - 2 * c.K, tymax = c.BG * c.R - 2 * c.K;
+    const int ntx_min = (n0 + txmax - 1) / txmax, nty_min = (n1 + tymax - 1) / tymax;
+    if (slots < 1 || ntx_min * nty_min > slots) return false;
+    long best_area = -1;
+    for (int tx_n = ntx_min; tx_n <= n0 && tx_n <= slots; ++tx_n) {
+        const int ty_n_max = slots / tx_n;
+        if (ty_n_max < nty_min) break;
+        for (int ty_n = nty_min; ty_n <= ty_n_max && ty_n <= n1; ++ty_n) {
+            const int a = (n0 + tx_n - 1) / tx_n, b = (n1 + ty_n - 1) / ty_n;
+            const long area = (long)(a + 2 * c.K) * (b + 2 * c.K);   // region per CTA
+            if (best_area < 0 || area < best_area) {
+                best_area = area;
+                *txo = a;
+                *tyo = b;
+                *ntx = (n0 + a - 1) / a;
+                *nty = (n1 + b - 1) / b;
+            }
+        }
+    }
+    return best_area > 0;
+}
+
+template <typename S>
+cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef, const float *kappa,
+                             float2 zfac, float h2, const float *tau_dev, int npass,
+                             int pass_per_sub, float2 rho, unsigned *bar, int txo, int tyo,
+                             int ntx, int nty, const S *x, S *ex0, S *ex1, S *out, cudaStream_t st)
+{
+    void *fn;
+    size_t smem;
+    cfg_info<S>(id, &fn, &smem);
+    PersistArgs a;
+    a.n0 = g.n[0];
+    a.n1 = g.n[1];
+    a.nmax = g.nmax;
+    a.npml = npml;
+    a.txo = txo;
+    a.tyo = tyo;
+    a.ntx = ntx;
+    a.nty = nty;
+    a.coef = coef;
+    a.kappa = kappa;
+    a.zfac = zfac;
+    a.h2 = h2;
+    a.tau = tau_dev;
+    a.npass = npass;
+    a.pass_per_sub = pass_per_sub;
+    a.rho = rho;
+    a.bar = bar;
+    void *args[] = {&a, (void *)&x, (void *)&ex0, (void *)&ex1, (void *)&out};
+    const PCfg c = kPCfgs[id];
+    cudaError_t e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    return cudaLaunchCooperativeKernel(fn, dim3(ntx * nty), dim3(c.BX * c.BG), args, smem, st);
+}
+
+#define MXP_PINST(S)                                                                          \
+    template bool persist2d_plan<S>(int, int, int, int, int *, int *, int *, int *);          \
+    template cudaError_t launch_persist2d<S>(int, const Geom &, int, const float2 *, const float *, \
+                                             float2, float, const float *, int, int, float2,  \
+                                             unsigned *, int, int, int, int, const S *, S *,  \
+                                             S *, S *, cudaStream_t);
+MXP_PINST(float2)
+MXP_PINST(__nv_bfloat162)
+#undef MXP_PINST
+
+}  // namespace mxp

@@ -40,7 +40,7 @@ class Params(ct.Structure):
                 ("t", ct.c_double), ("fprtol", ct.c_double), ("exp_tol", ct.c_double),
                 ("inner_restart", ct.c_int), ("inner_maxit", ct.c_int),
                 ("inner_fixed", ct.c_int), ("prec", ct.c_int), ("theta_max", ct.c_double),
-                ("fuse_k", ct.c_int), ("tile_cfg", ct.c_int)]
+                ("fuse_k", ct.c_int), ("tile_cfg", ct.c_int), ("persist_cfg", ct.c_int)]
 
 
 class ApplyStats(ct.Structure):
@@ -89,6 +89,7 @@ SIGNATURES = {
     "mxp_kernel_launch_count": (ct.c_int64, []),
     "mxp_num_tile_configs": (ct.c_int, []),
     "mxp_tile_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
+    "mxp_persist_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_destroy": (None, [ct.c_void_p]),
     "mxp_status_string": (ct.c_char_p, [ct.c_int]),
     "mxp_last_error": (ct.c_char_p, []),
@@ -209,6 +210,12 @@ class Problem:
         """(configuration index or -1 for the unfused sweep, fused step count)."""
         k = ct.c_int(0)
         cfg = self._lib.mxp_tile_config(self._h, ct.byref(k))
+        return int(cfg), int(k.value)
+
+    def persist_config(self):
+        """(persistent exp kernel configuration or -1, number of tiles)."""
+        k = ct.c_int(0)
+        cfg = self._lib.mxp_persist_config(self._h, ct.byref(k))
         return int(cfg), int(k.value)
 
     # -- operations (all on the problem's stream)
