@@ -200,6 +200,33 @@ int mxp_tile_config(const mxp_problem *prob, int *fuse_k);
 /* Persistent exp-action kernel in use (-1 = none) and its tile count. */
 int mxp_persist_config(const mxp_problem *prob, int *ntiles);
 
+/* Allocation-free exp / psi_1 action.  The paper has no counterpart: this is
+ * a service for callers that cannot allocate device memory when they need an
+ * action -- code running while a CUDA graph is being captured, plugins whose
+ * host application owns all device memory through its own pool, or loops that
+ * cannot afford a cudaMalloc (which may synchronise the device).
+ *
+ * Computes y = exp(i t A_s) x (which = 0) or y = psi_1(i t A_s) x (which = 1)
+ * in complex128 exactly like mxp_apply_phi with prec = MXP_C128, without a
+ * problem handle: grid and params (omega, c_pml, shift_s, t, exp_tol,
+ * theta_max; the other fields are ignored) describe the problem, c_dev is the
+ * wave speed on the device (prod_d n_d doubles, x fastest, finite and > 0),
+ * x_dev / y_dev are caller-owned complex128 device vectors (not aliased), work
+ * is ordered on cuda_stream (NULL = legacy default stream), and the stream is
+ * synchronised once during the call (to read the range of c).
+ *
+ * All workspace lives in one fixed device array compiled into the library:
+ * at most 262,144 unknowns, 4,096 unknowns per axis and 64 PML cells per side
+ * (about 16 MB, held by every GPU that loads the library until the process
+ * exits).  Larger grids return MXP_EINVAL with a message in mxp_last_error().
+ * The call makes no device allocation.  Calls share the array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must be
+ * ordered by the caller.  The first call on a device looks up the array's
+ * address and should come before any stream capture begins. */
+mxp_status mxp_apply_phi_noalloc(const mxp_grid *grid, const mxp_params *params,
+                                 const double *c_dev, int which, const void *x_dev,
+                                 void *y_dev, void *cuda_stream, int64_t *passes_out);
+
 /* Number of unknowns prod_d n_d of the problem. */
 int64_t mxp_num_unknowns(const mxp_problem *prob);
 

@@ -32,6 +32,8 @@ using cd = std::complex<double>;
 
 static thread_local std::string g_last_error;
 
+void mxp::note_error(const char *msg) { g_last_error = msg; }
+
 static mxp_status fail(mxp_status s, const std::string &msg)
 {
     g_last_error = msg;

@@ -12,6 +12,9 @@
 
 namespace mxp {
 
+// Record a message for mxp_last_error() (thread-local).
+void note_error(const char *msg);
+
 // Number of kernels this library has launched (process-wide).
 extern std::atomic<long long> g_launch_count;
 inline void count_launch(int n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }

@@ -85,6 +85,9 @@ SIGNATURES = {
                                    ct.POINTER(ct.c_int), ct.POINTER(ct.c_void_p),
                                    ct.POINTER(ct.c_void_p), ct.POINTER(SolveOpts),
                                    ct.POINTER(SolveStats)]),
+    "mxp_apply_phi_noalloc": (ct.c_int, [ct.POINTER(Grid), ct.POINTER(Params),
+                                         ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
+                                         ct.c_void_p, ct.POINTER(ct.c_int64)]),
     "mxp_num_unknowns": (ct.c_int64, [ct.c_void_p]),
     "mxp_kernel_launch_count": (ct.c_int64, []),
     "mxp_num_tile_configs": (ct.c_int, []),
