@@ -110,6 +110,18 @@ struct mxp_problem {
     float *tau_dev = nullptr;  // per-step tau / h^2 of the exp plan (persistent kernel)
     size_t tau_cap = 0;
     unsigned *bar = nullptr;   // grid-barrier words of the persistent kernel
+    // batched solves (several right-hand sides of this problem in lockstep)
+    struct Rhs {
+        Arnoldi outer, inner;
+        double2 *rt = nullptr, *r = nullptr;
+    };
+    std::vector<Rhs> rhs;
+    int bcap = 0;                         // batch slots allocated
+    void *bslot[4] = {nullptr, nullptr, nullptr, nullptr};   // bcap vectors each, 16 B per unknown
+    double *bhost = nullptr;              // pinned, 8 doubles per right-hand side
+    std::map<long long, cudaGraphExec_t> graphs;   // captured pass sequences
+    cudaStream_t cap_stream = nullptr;    // private stream the sweep sequences are captured on
+    TaylorPlan bplan_exp, bplan_psi;      // plans of the batched (per-pass fused) sweeps
     // workspace
     void *hb[4] = {nullptr, nullptr, nullptr, nullptr};   // 16 bytes per unknown each
     double2 *rt = nullptr, *tmp = nullptr, *tmp2 = nullptr;
@@ -952,6 +964,412 @@ static mxp_status fgmres_solve(mxp_problem *P, const double2 *b, double2 *x, con
     return MXP_OK;
 }
 
+
+// ------------------------------------------------------------------ batched solves
+// Several right-hand sides of one problem advance in lockstep: their outer
+// FGMRES and inner GMRES iterations run side by side, and every exp / psi_1
+// action of the active right-hand sides is one sequence of sweeps over the
+// whole batch (one launch per pass covers all vectors).  Each sweep sequence
+// is captured once as a CUDA graph per (action, batch size, plan) and replayed.
+// Right-hand sides that have converged leave the batch.
+
+static void clear_graphs(mxp_problem *P)
+{
+    for (auto &kv : P->graphs) cudaGraphExecDestroy(kv.second);
+    P->graphs.clear();
+}
+
+static void free_batch(mxp_problem *P)
+{
+    clear_graphs(P);
+    if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+    P->cap_stream = nullptr;
+    for (auto &r : P->rhs) {
+        free_arnoldi(r.outer);
+        free_arnoldi(r.inner);
+        cudaFree(r.rt);
+        cudaFree(r.r);
+    }
+    P->rhs.clear();
+    for (int i = 0; i < 4; ++i) { cudaFree(P->bslot[i]); P->bslot[i] = nullptr; }
+    if (P->bhost) cudaFreeHost(P->bhost);
+    P->bhost = nullptr;
+    P->bcap = 0;
+}
+
+static mxp_status ensure_batch(mxp_problem *P, int nr, int Rout, int Rin)
+{
+    const int64_t n = P->ntot;
+    if (nr > P->bcap) {
+        clear_graphs(P);
+        for (int i = 0; i < 4; ++i) { cudaFree(P->bslot[i]); P->bslot[i] = nullptr; }
+        if (P->bhost) cudaFreeHost(P->bhost);
+        P->bhost = nullptr;
+        for (int i = 0; i < 4; ++i) CK(cudaMalloc(&P->bslot[i], (size_t)nr * n * 16));
+        CK(cudaMallocHost(&P->bhost, (size_t)nr * 8 * sizeof(double)));
+        P->bcap = nr;
+    }
+    if ((int)P->rhs.size() < nr) P->rhs.resize(nr);
+    for (int r = 0; r < nr; ++r) {
+        auto &s = P->rhs[r];
+        CKS(ensure_arnoldi(P, s.outer, Rout, true));
+        CKS(ensure_arnoldi(P, s.inner, Rin, false));
+        if (!s.rt) CK(cudaMalloc(&s.rt, n * sizeof(double2)));
+        if (!s.r) CK(cudaMalloc(&s.r, n * sizeof(double2)));
+    }
+    return MXP_OK;
+}
+
+// Launch the Horner sweeps of one action over nb batch vectors held in the
+// batch slots (input in slot 0, psi_1 source in slot 3).  Returns the slot
+// holding the result.
+template <typename S>
+static int batch_sweeps(mxp_problem *P, int which, int nb, const TaylorPlan &pl, int64_t *passes,
+                        cudaStream_t st)
+{
+    using C = typename St<S>::C;
+    const int64_t n = P->ntot;
+    S *b[3] = {(S *)P->bslot[0], (S *)P->bslot[1], (S *)P->bslot[2]};
+    S *vs = which ? (S *)P->bslot[3] : nullptr;
+    const double t = P->prm.t;
+    const int Ssub = pl.S, m = pl.m;
+    const cd rot(0.0, -t * P->mu / Ssub);
+    const cd final_rho = std::exp(cd(0.0, t * P->mu));
+    const int cfg = (sizeof(S) <= 8 && P->grid.dim == 2) ? P->fused_cfg : -1;
+    const int K = cfg >= 0 ? fused2d_cfg_k(cfg) : 1;
+    cd yxi = which ? cd(1.0) : cd(0.0);
+    int iy = 0;
+    StepScalars<C> sc;
+    sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
+    sc.mu = (sizeof(S) <= 8) ? (typename St<S>::R)0 : (typename St<S>::R)P->mu;
+    for (int sub = 0; sub < Ssub; ++sub) {
+        int in = iy;
+        cd pxi = yxi;
+        for (int k = m; k >= 1; k -= K) {
+            const int o = (in == iy) ? (iy + 1) % 3 : 3 - iy - in;
+            if (cfg >= 0) {
+                FusedStep steps[kMaxFuse];
+                for (int s = 0; s < K; ++s) {
+                    const int kk = k - s;
+                    const cd gam = which ? pxi / ((double)Ssub * kk) : cd(0.0);
+                    steps[s] = FusedStep{t / ((double)Ssub * kk), gam.real(), gam.imag(), final_rho.real(),
+                                         final_rho.imag(), (sub == Ssub - 1 && kk == 1) ? 1 : 0};
+                    pxi = yxi + rot * pxi / (double)kk;
+                }
+                launch_fused2d<S>(cfg, P->fused_tyo, P->geom, P->grid.npml, P->coef32, P->kappa32, steps,
+                                  make_float2(1.0f, (float)P->prm.shift_s), 0.0f,
+                                  (float)(1.0 / (P->grid.h * P->grid.h)), b[in], b[iy], vs, b[o], st, nb);
+            } else {
+                sc.sigma = PrecData<S>::c(cd(0.0, t / ((double)Ssub * k)));
+                sc.gamma = PrecData<S>::c(which ? pxi / ((double)Ssub * k) : cd(0.0));
+                sc.rho = PrecData<S>::c((sub == Ssub - 1 && k == 1) ? final_rho : cd(1.0));
+                for (int j = 0; j < nb; ++j)
+                    launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc, b[in] + j * n,
+                                   b[iy] + j * n, vs ? vs + j * n : nullptr, b[o] + j * n, st);
+                pxi = yxi + rot * pxi / (double)k;
+            }
+            in = o;
+            *passes += K;
+        }
+        iy = in;
+        yxi = pxi;
+    }
+    return iy;
+}
+
+// out[j] = exp(i t A_s) in[j] (which 0) or psi_1(i t A_s) in[j] (which 1), or
+// in[j] - that (out_mode 1), for j < nb; vectors complex128.
+template <typename S>
+static mxp_status phi_batch_t(mxp_problem *P, int which, int nb, const double2 *const *in,
+                              double2 *const *out, int out_mode, int64_t *passes_out)
+{
+    const int64_t n = P->ntot;
+    cudaStream_t st = P->stream;
+    const int K = (sizeof(S) <= 8 && P->grid.dim == 2 && P->fused_cfg >= 0) ? fused2d_cfg_k(P->fused_cfg) : 1;
+    const TaylorPlan pl = which ? P->plan_psi
+                                : make_plan(P->nu, P->prm.exp_tol, theta_of(P), K);
+    S *b0 = (S *)P->bslot[0], *vs = (S *)P->bslot[3];
+    for (int j = 0; j < nb; ++j) {
+        if (which == 0) launch_convert_in<S>(in[j], b0 + j * n, n, st);
+        else launch_convert_in<S>(in[j], vs + j * n, n, st);
+    }
+    if (which == 1) CK(cudaMemsetAsync(b0, 0, (size_t)nb * n * sizeof(S), st));
+    const long long key = ((((long long)which * 4096 + nb) * 65536 + pl.S) * 1024 + pl.m) * 64 + K;
+    int64_t passes = 0;
+    int fin = -1;
+    auto it = P->graphs.find(key);
+    if (it != P->graphs.end()) CK(cudaGraphLaunch(it->second, st));
+    if (it == P->graphs.end()) {
+        // first time: record the sweep sequence on the private capture stream
+        // (the problem's stream may be the legacy stream, which cannot be
+        // captured), instantiate it and launch it on the problem's stream; if
+        // capture is unavailable the sweeps run once, directly
+        if (!P->cap_stream) CK(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+        const long long l0 = g_launch_count.load();
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        bool ok = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            fin = batch_sweeps<S>(P, which, nb, pl, &passes, P->cap_stream);
+            ok = cudaStreamEndCapture(P->cap_stream, &graph) == cudaSuccess && graph &&
+                 cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+            if (graph) cudaGraphDestroy(graph);
+        }
+        if (ok) {
+            P->graphs[key] = exec;
+            CK(cudaGraphLaunch(exec, st));
+        } else {
+            cudaGetLastError();
+            g_launch_count.store(l0);
+            passes = 0;
+            fin = batch_sweeps<S>(P, which, nb, pl, &passes, st);   // nothing ran yet: run once
+        }
+    } else {
+        // the replayed graph holds the sweeps: recompute the result slot, the
+        // pass count and the kernel count without launching
+        const int cfg = (sizeof(S) <= 8 && P->grid.dim == 2) ? P->fused_cfg : -1;
+        const int KK = cfg >= 0 ? fused2d_cfg_k(cfg) : 1;
+        int iy = 0;
+        for (int sub = 0; sub < pl.S; ++sub) {
+            int in2 = iy;
+            for (int k = pl.m; k >= 1; k -= KK) {
+                in2 = (in2 == iy) ? (iy + 1) % 3 : 3 - iy - in2;
+                passes += KK;
+            }
+            iy = in2;
+        }
+        fin = iy;
+        const int per = (cfg >= 0) ? 1 : nb;
+        count_launch((int)((passes / KK) * per));
+    }
+    S *res = (S *)P->bslot[fin];
+    for (int j = 0; j < nb; ++j) launch_convert_out<S>(res + j * n, out[j], in[j], out_mode, n, st);
+    CK(cudaGetLastError());
+    P->passes += passes * nb;
+    if (passes_out) *passes_out = passes;
+    return MXP_OK;
+}
+
+static mxp_status phi_batch(mxp_problem *P, int which, int nb, const double2 *const *in,
+                            double2 *const *out, int out_mode, int64_t *passes)
+{
+    switch (P->prm.prec) {
+    case MXP_C64: return phi_batch_t<float2>(P, which, nb, in, out, out_mode, passes);
+    case MXP_BF16S: return phi_batch_t<__nv_bfloat162>(P, which, nb, in, out, out_mode, passes);
+    default: return phi_batch_t<double2>(P, which, nb, in, out, out_mode, passes);
+    }
+}
+
+// Read scal[0..cnt) of every listed right-hand side's Arnoldi state into
+// bhost[8*i ...], one synchronisation.
+static mxp_status read_batch(mxp_problem *P, const std::vector<int> &ids, bool outer, int first, int cnt)
+{
+    for (size_t i = 0; i < ids.size(); ++i) {
+        const Arnoldi &a = outer ? P->rhs[ids[i]].outer : P->rhs[ids[i]].inner;
+        CK(cudaMemcpyAsync(P->bhost + 8 * i, a.hs.scal + first, cnt * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+    }
+    CK(cudaStreamSynchronize(P->stream));
+    return MXP_OK;
+}
+
+// Algorithm 1 for the listed right-hand sides in lockstep: out[i] = MatExPre(in[i]).
+// The inner GMRES of each one stops at fprtol (or inner_fixed iterations) and,
+// in this batched form, after at most inner_restart iterations (no restart).
+static mxp_status batch_matexpre(mxp_problem *P, const std::vector<int> &ids, const std::vector<const double2 *> &in,
+                                 const std::vector<double2 *> &out, std::vector<int> &inner_iters)
+{
+    const int nb = (int)ids.size();
+    const int64_t n = P->ntot;
+    cudaStream_t st = P->stream;
+    const int R = P->prm.inner_restart;
+    std::vector<double2 *> rts(nb);
+    for (int i = 0; i < nb; ++i) rts[i] = P->rhs[ids[i]].rt;
+    CKS(phi_batch(P, 1, nb, in.data(), rts.data(), 0, nullptr));
+    for (int i = 0; i < nb; ++i) {
+        Arnoldi &a = P->rhs[ids[i]].inner;
+        CK(cudaMemsetAsync(out[i], 0, n * sizeof(double2), st));
+        krylov_nrm2sq(rts[i], n, a.hs.scal, P->ks, st);
+        hess_start(a.hs, st);
+        krylov_scale_invnorm(a.V, rts[i], a.hs.scal, n, st);
+    }
+    CKS(read_batch(P, ids, false, 3, 1));
+    std::vector<double> zeta(nb);
+    std::vector<int> jj(nb, 0);
+    std::vector<char> active(nb, 1);
+    for (int i = 0; i < nb; ++i) {
+        zeta[i] = P->bhost[8 * i];
+        if (!std::isfinite(zeta[i])) return fail(MXP_ENAN, "psi_1(i t A_s) r is not finite");
+        if (zeta[i] == 0.0) active[i] = 0;
+    }
+    const int fixed = P->prm.inner_fixed;
+    const int jmax = std::min(R, fixed > 0 ? fixed : P->prm.inner_maxit);
+    for (int j = 0; j < jmax; ++j) {
+        std::vector<int> act;
+        std::vector<const double2 *> vin;
+        std::vector<double2 *> vout;
+        for (int i = 0; i < nb; ++i)
+            if (active[i]) {
+                Arnoldi &a = P->rhs[ids[i]].inner;
+                act.push_back(i);
+                vin.push_back(a.V + (size_t)j * n);
+                vout.push_back(a.V + (size_t)(j + 1) * n);
+            }
+        if (act.empty()) break;
+        CKS(phi_batch(P, 0, (int)act.size(), vin.data(), vout.data(), 1, nullptr));
+        std::vector<int> act_ids;
+        for (int i : act) {
+            arnoldi_step(P, P->rhs[ids[i]].inner, j);
+            act_ids.push_back(ids[i]);
+        }
+        CK(cudaGetLastError());
+        CKS(read_batch(P, act_ids, false, 1, 2));
+        for (size_t q = 0; q < act.size(); ++q) {
+            const int i = act[q];
+            const double est = P->bhost[8 * q], brk = P->bhost[8 * q + 1];
+            if (!std::isfinite(est)) return fail(MXP_ENAN, "inner GMRES residual is not finite");
+            jj[i] = j + 1;
+            if (brk != 0.0 || (fixed <= 0 && est <= P->prm.fprtol * zeta[i])) active[i] = 0;
+        }
+    }
+    for (int i = 0; i < nb; ++i) {
+        inner_iters[i] = jj[i];
+        if (jj[i] == 0) continue;
+        Arnoldi &a = P->rhs[ids[i]].inner;
+        hess_backsolve(a.hs, jj[i], st);
+        krylov_maxpy(out[i], a.V, n, jj[i], a.hs.y, 1.0, n, st);
+    }
+    CK(cudaGetLastError());
+    return MXP_OK;
+}
+
+// Outer FGMRES for nr right-hand sides of one problem in lockstep.
+static mxp_status batch_solve(mxp_problem *P, int nr, const double2 *const *b, double2 *const *x,
+                              const mxp_solve_opts *o, mxp_solve_stats *stats)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    CKS(ensure_base(P));
+    const int R = o->restart;
+    CKS(ensure_batch(P, nr, R, P->prm.inner_restart));
+    const int64_t n = P->ntot;
+    cudaStream_t st = P->stream;
+    const int64_t passes0 = P->passes;
+    std::vector<int> all(nr);
+    for (int r = 0; r < nr; ++r) all[r] = r;
+    for (int r = 0; r < nr; ++r) krylov_nrm2sq(b[r], n, P->rhs[r].outer.hs.scal, P->ks, st);
+    CKS(read_batch(P, all, true, 0, 1));
+    std::vector<double> bnorm(nr), relres(nr, 1.0), est(nr, 0.0);
+    std::vector<int> total(nr, 0), inner_total(nr, 0), jr(nr, 0);
+    std::vector<char> done(nr, 0), conv(nr, 0);
+    for (int r = 0; r < nr; ++r) {
+        bnorm[r] = std::sqrt(P->bhost[8 * r]);
+        if (!std::isfinite(bnorm[r])) return fail(MXP_ENAN, "right-hand side is not finite");
+        if (!o->x0_given) {
+            CK(cudaMemsetAsync(x[r], 0, n * sizeof(double2), st));
+            krylov_copy(P->rhs[r].r, b[r], n, st);
+        } else {
+            apply_op(P, 0, x[r], P->rhs[r].r);
+            krylov_sub(P->rhs[r].r, b[r], P->rhs[r].r, n, st);
+        }
+        if (bnorm[r] == 0.0) {
+            CK(cudaMemsetAsync(x[r], 0, n * sizeof(double2), st));
+            done[r] = conv[r] = 1;
+            relres[r] = 0;
+        }
+    }
+    while (true) {
+        std::vector<int> live;
+        for (int r = 0; r < nr; ++r)
+            if (!done[r]) live.push_back(r);
+        if (live.empty()) break;
+        // cycle start: V0 = r / beta
+        for (int r : live) {
+            Arnoldi &a = P->rhs[r].outer;
+            krylov_nrm2sq(P->rhs[r].r, n, a.hs.scal, P->ks, st);
+            hess_start(a.hs, st);
+            krylov_scale_invnorm(a.V, P->rhs[r].r, a.hs.scal, n, st);
+        }
+        CKS(read_batch(P, live, true, 3, 1));
+        std::vector<int> cyc;
+        for (size_t q = 0; q < live.size(); ++q) {
+            const int r = live[q];
+            const double beta = P->bhost[8 * q];
+            if (!std::isfinite(beta)) return fail(MXP_ENAN, "outer residual is not finite");
+            relres[r] = beta / bnorm[r];
+            jr[r] = 0;
+            if (beta <= o->rtol * bnorm[r]) { done[r] = conv[r] = 1; continue; }
+            if (total[r] >= o->maxit) { done[r] = 1; continue; }
+            cyc.push_back(r);
+        }
+        if (cyc.empty()) continue;
+        std::vector<char> stop(nr, 0);
+        for (int j = 0; j < R; ++j) {
+            std::vector<int> act;
+            for (int r : cyc)
+                if (!stop[r] && total[r] < o->maxit) act.push_back(r);
+            if (act.empty()) break;
+            std::vector<const double2 *> vin;
+            std::vector<double2 *> zout;
+            for (int r : act) {
+                vin.push_back(P->rhs[r].outer.V + (size_t)j * n);
+                zout.push_back(P->rhs[r].outer.Z + (size_t)j * n);
+            }
+            std::vector<int> inn(act.size(), 0);
+            CKS(batch_matexpre(P, act, vin, zout, inn));
+            for (size_t q = 0; q < act.size(); ++q) {
+                const int r = act[q];
+                inner_total[r] += inn[q];
+                Arnoldi &a = P->rhs[r].outer;
+                apply_op(P, 0, a.Z + (size_t)j * n, a.V + (size_t)(j + 1) * n);
+                arnoldi_step(P, a, j);
+            }
+            CK(cudaGetLastError());
+            CKS(read_batch(P, act, true, 1, 2));
+            for (size_t q = 0; q < act.size(); ++q) {
+                const int r = act[q];
+                est[r] = P->bhost[8 * q];
+                if (!std::isfinite(est[r])) return fail(MXP_ENAN, "outer FGMRES residual is not finite");
+                ++total[r];
+                jr[r] = j + 1;
+                if (P->bhost[8 * q + 1] != 0.0 || est[r] <= o->rtol * bnorm[r]) stop[r] = 1;
+            }
+        }
+        for (int r : cyc) {
+            Arnoldi &a = P->rhs[r].outer;
+            hess_backsolve(a.hs, jr[r], st);
+            krylov_maxpy(x[r], a.Z, n, jr[r], a.hs.y, 1.0, n, st);
+            apply_op(P, 0, x[r], P->rhs[r].r);
+            krylov_sub(P->rhs[r].r, b[r], P->rhs[r].r, n, st);
+            krylov_nrm2sq(P->rhs[r].r, n, a.hs.scal + 4, P->ks, st);
+        }
+        CKS(read_batch(P, cyc, true, 4, 1));
+        for (size_t q = 0; q < cyc.size(); ++q) {
+            const int r = cyc[q];
+            relres[r] = std::sqrt(P->bhost[8 * q]) / bnorm[r];
+            if (!std::isfinite(relres[r])) return fail(MXP_ENAN, "true residual is not finite");
+            if (relres[r] <= o->rtol) done[r] = conv[r] = 1;
+            else if (total[r] >= o->maxit) done[r] = 1;
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    bool all_conv = true;
+    for (int r = 0; r < nr; ++r) {
+        all_conv = all_conv && conv[r];
+        if (stats) {
+            stats[r].outer_iters = total[r];
+            stats[r].inner_iters_total = inner_total[r];
+            stats[r].converged = conv[r];
+            stats[r].true_relres = relres[r];
+            stats[r].est_relres = bnorm[r] > 0 ? est[r] / bnorm[r] : 0.0;
+            stats[r].stencil_passes = (P->passes - passes0) / std::max(nr, 1);
+            stats[r].pt_updates = (P->passes - passes0) * n / std::max(nr, 1);
+            stats[r].seconds = secs;
+        }
+    }
+    if (!all_conv) return fail(MXP_ENOCONV, "outer FGMRES reached maxit for a right-hand side");
+    return MXP_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -1075,6 +1493,7 @@ mxp_status mxp_set_params(mxp_problem *P, const mxp_params *p)
     if (recoef) CKS(upload_coefs(P));
     update_plans(P);
     CKS(upload_coef32(P));
+    clear_graphs(P);
     return retune(P);
 }
 
@@ -1180,17 +1599,32 @@ mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs, const
         return fail(MXP_EINVAL, "invalid batch arguments");
     CKS(check_opts(opts));
     for (int r = 0; r < nrhs; ++r)
-        if (prob_of_rhs[r] < 0 || prob_of_rhs[r] >= nprob || !probs[prob_of_rhs[r]] || !b_dev[r] || !x_dev[r])
+        if (prob_of_rhs[r] < 0 || prob_of_rhs[r] >= nprob || !probs[prob_of_rhs[r]] || !b_dev[r] || !x_dev[r] ||
+            b_dev[r] == x_dev[r])
             return fail(MXP_EINVAL, "invalid right-hand side entry");
     mxp_status worst = MXP_OK;
-    for (int r = 0; r < nrhs; ++r) {
-        mxp_solve_stats s{};
-        mxp_status e = mxp_solve(probs[prob_of_rhs[r]], b_dev[r], x_dev[r], opts, &s);
-        if (per_rhs) per_rhs[r] = s;
+    for (int pi = 0; pi < nprob; ++pi) {
+        std::vector<int> idx;
+        for (int r = 0; r < nrhs; ++r)
+            if (prob_of_rhs[r] == pi) idx.push_back(r);
+        if (idx.empty()) continue;
+        mxp_problem *P = probs[pi];
+        DeviceGuard guard(P->device);
+        std::vector<const double2 *> bs;
+        std::vector<double2 *> xs;
+        for (int r : idx) {
+            bs.push_back((const double2 *)b_dev[r]);
+            xs.push_back((double2 *)x_dev[r]);
+        }
+        std::vector<mxp_solve_stats> st(idx.size());
+        mxp_status e = batch_solve(P, (int)idx.size(), bs.data(), xs.data(), opts, st.data());
+        if (per_rhs)
+            for (size_t q = 0; q < idx.size(); ++q) per_rhs[idx[q]] = st[q];
         if (e != MXP_OK && e != MXP_ENOCONV) return e;
         if (e == MXP_ENOCONV) worst = e;
     }
-    return worst;
+    if (worst == MXP_ENOCONV) return fail(MXP_ENOCONV, "a right-hand side did not converge");
+    return MXP_OK;
 }
 
 void mxp_destroy(mxp_problem *P)
@@ -1208,6 +1642,7 @@ void mxp_destroy(mxp_problem *P)
     if (P->host_scal) cudaFreeHost(P->host_scal);
     free_arnoldi(P->inner);
     free_arnoldi(P->outer);
+    free_batch(P);
     delete P;
 }
 

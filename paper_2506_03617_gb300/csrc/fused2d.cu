@@ -44,6 +44,14 @@ __global__ void __launch_bounds__(RX *G, (RX * G <= 512 && !HAS_V) ? 2 : 1) k_fu
     constexpr int PX = RX + 2;                 // padded row (zero column on each side)
     // output tile TXO x TYO (<= RX-2K x RY-2K, chosen at run time); region = tile + K halo
     extern __shared__ float2 sm[];
+    // blockIdx.z selects one vector of a batch (vectors of one grid, n0*n1 apart)
+    {
+        const int64_t off = (int64_t)blockIdx.z * n0 * n1;
+        pin += off;
+        yv_g += off;
+        if (HAS_V) v_g += off;
+        pout += off;
+    }
     float2 *buf0 = sm;
     float2 *buf1 = sm + (RY + 2) * PX;
     float2 *cy = buf1 + (RY + 2) * PX;         // [RY][2]: wp_y, wm_y of each region row
@@ -187,7 +195,7 @@ int fused2d_num_cfgs() { return kNumCfgs; }
 int fused2d_cfg_k(int id) { return kCfgs[id].K; }
 
 template <typename S, int K, int RX, int RT, int G, bool HAS_V>
-static void launch_one(int n0, int n1, int npml, int nmax, int tyo, const float2 *coef,
+static void launch_one(int n0, int n1, int npml, int nmax, int tyo, int nb, const float2 *coef,
                        const float *kappa, const FusedScalars &sc, const S *pin, const S *y,
                        const S *v, S *pout, cudaStream_t st)
 {
@@ -203,19 +211,19 @@ static void launch_one(int n0, int n1, int npml, int nmax, int tyo, const float2
     const int ntx = (n0 + RX - 2 * K - 1) / (RX - 2 * K);
     const int txo = (n0 + ntx - 1) / ntx;
     if (tyo <= 0 || tyo > RY - 2 * K) tyo = RY - 2 * K;
-    dim3 grid(ntx, (n1 + tyo - 1) / tyo);
+    dim3 grid(ntx, (n1 + tyo - 1) / tyo, nb);
     count_launch();
     k_fused2d<S, K, RX, RT, G, HAS_V><<<grid, RX * G, smem, st>>>(n0, n1, npml, nmax, txo, tyo,
                                                                  coef, kappa, sc, pin, y, v, pout);
 }
 
 template <typename S, int K, int RX, int RT, int G>
-static void launch_v(bool hv, int n0, int n1, int npml, int nmax, int tyo, const float2 *coef,
-                     const float *kappa, const FusedScalars &sc, const S *pin, const S *y,
-                     const S *v, S *pout, cudaStream_t st)
+static void launch_v(bool hv, int n0, int n1, int npml, int nmax, int tyo, int nb,
+                     const float2 *coef, const float *kappa, const FusedScalars &sc, const S *pin,
+                     const S *y, const S *v, S *pout, cudaStream_t st)
 {
-    if (hv) launch_one<S, K, RX, RT, G, true>(n0, n1, npml, nmax, tyo, coef, kappa, sc, pin, y, v, pout, st);
-    else launch_one<S, K, RX, RT, G, false>(n0, n1, npml, nmax, tyo, coef, kappa, sc, pin, y, v, pout, st);
+    if (hv) launch_one<S, K, RX, RT, G, true>(n0, n1, npml, nmax, tyo, nb, coef, kappa, sc, pin, y, v, pout, st);
+    else launch_one<S, K, RX, RT, G, false>(n0, n1, npml, nmax, tyo, nb, coef, kappa, sc, pin, y, v, pout, st);
 }
 
 int fused2d_cfg_rx(int id) { return kCfgs[id].RX; }
@@ -224,7 +232,7 @@ int fused2d_cfg_max_tyo(int id) { return kCfgs[id].RT * kCfgs[id].G - 2 * kCfgs[
 template <typename S>
 bool launch_fused2d(int cfg, int tyo, const Geom &g, int npml, const float2 *coef, const float *kappa,
                     const FusedStep *steps, const float2 zfac, float mu, float ih2,
-                    const S *pin, const S *y, const S *v, S *pout, cudaStream_t st)
+                    const S *pin, const S *y, const S *v, S *pout, cudaStream_t st, int nb)
 {
     if (g.dim != 2 || cfg < 0 || cfg >= kNumCfgs) return false;
     FusedScalars sc;
@@ -245,14 +253,14 @@ bool launch_fused2d(int cfg, int tyo, const Geom &g, int npml, const float2 *coe
     const bool hv = (v != nullptr);
     const int n0 = g.n[0], n1 = g.n[1], nm = g.nmax;
     switch (cfg) {
-    case 0: launch_v<S, 2, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 1: launch_v<S, 4, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 2: launch_v<S, 8, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 3: launch_v<S, 4, 64, 4, 8>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 4: launch_v<S, 2, 64, 4, 8>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 5: launch_v<S, 8, 128, 12, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 6: launch_v<S, 4, 128, 4, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
-    case 7: launch_v<S, 6, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 0: launch_v<S, 2, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, nb, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 1: launch_v<S, 4, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, nb, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 2: launch_v<S, 8, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, nb, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 3: launch_v<S, 4, 64, 4, 8>(hv, n0, n1, npml, nm, tyo, nb, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 4: launch_v<S, 2, 64, 4, 8>(hv, n0, n1, npml, nm, tyo, nb, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 5: launch_v<S, 8, 128, 12, 4>(hv, n0, n1, npml, nm, tyo, nb, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 6: launch_v<S, 4, 128, 4, 4>(hv, n0, n1, npml, nm, tyo, nb, coef, kappa, sc, pin, y, v, pout, st); break;
+    case 7: launch_v<S, 6, 128, 8, 4>(hv, n0, n1, npml, nm, tyo, nb, coef, kappa, sc, pin, y, v, pout, st); break;
     default: return false;
     }
     return true;
@@ -260,10 +268,10 @@ bool launch_fused2d(int cfg, int tyo, const Geom &g, int npml, const float2 *coe
 
 template bool launch_fused2d<float2>(int, int, const Geom &, int, const float2 *, const float *,
                                      const FusedStep *, const float2, float, float, const float2 *,
-                                     const float2 *, const float2 *, float2 *, cudaStream_t);
+                                     const float2 *, const float2 *, float2 *, cudaStream_t, int);
 template bool launch_fused2d<__nv_bfloat162>(int, int, const Geom &, int, const float2 *, const float *,
                                              const FusedStep *, const float2, float, float,
                                              const __nv_bfloat162 *, const __nv_bfloat162 *,
-                                             const __nv_bfloat162 *, __nv_bfloat162 *, cudaStream_t);
+                                             const __nv_bfloat162 *, __nv_bfloat162 *, cudaStream_t, int);
 
 }  // namespace mxp

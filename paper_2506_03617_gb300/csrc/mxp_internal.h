@@ -98,10 +98,11 @@ int fused2d_cfg_k(int cfg);
 int fused2d_cfg_max_tyo(int cfg);
 int fused2d_cfg_rx(int cfg);   // largest output-tile height of the configuration
 // tyo: output-tile height (<= fused2d_cfg_max_tyo; <= 0 selects the largest)
+// nb: batch of vectors of this grid stored n apart (blockIdx.z selects one)
 template <typename S>
 bool launch_fused2d(int cfg, int tyo, const Geom &g, int npml, const float2 *coef, const float *kappa,
                     const FusedStep *steps, const float2 zfac, float mu, float ih2,
-                    const S *pin, const S *y, const S *v, S *pout, cudaStream_t st);
+                    const S *pin, const S *y, const S *v, S *pout, cudaStream_t st, int nb = 1);
 
 // Persistent exp action (2D, float storage types): see persist2d.cu.
 int persist2d_num_cfgs();
