@@ -128,6 +128,8 @@ typedef struct {
     int64_t stencil_passes;    /* all stencil sweeps (actions + operator) */
     int64_t pt_updates;        /* sum over sweeps of the unknowns touched */
     double seconds;            /* wall time of the call (host clock) */
+    int nn_accepted;           /* learned-stage directions kept (mxp_attach_cnn) */
+    int nn_rejected;           /* learned-stage directions replaced by MatExPre */
 } mxp_solve_stats;
 
 typedef struct mxp_problem mxp_problem;   /* opaque, library-owned */
@@ -226,6 +228,40 @@ int mxp_persist_config(const mxp_problem *prob, int *ntiles);
 mxp_status mxp_apply_phi_noalloc(const mxp_grid *grid, const mxp_params *params,
                                  const double *c_dev, int which, const void *x_dev,
                                  void *y_dev, void *cuda_stream, int64_t *passes_out);
+
+/* ---------------------------------------------------------------- learned stage
+ * A six-layer U-Net-style CNN (bfloat16 weights, float32 accumulation) with
+ * GPU training and inference kernels, used as an extra FGMRES preconditioning
+ * stage with MatExPre as fallback.  The paper has no learned stage; this is an
+ * extension of this library.  Tensors are float32 NCHW device arrays: input
+ * channels (Re r, Im r, c / c_max) with r scaled to unit root-mean-square,
+ * output channels (Re z, Im z).  H and W must be even.
+ * Layers: 3->32 relu; 32->64 stride 2 relu; 64->64 relu; 64->64 relu;
+ * nearest x2 upsample then 64->32 relu plus the first layer's output (skip);
+ * 32->2.  Flat parameters (float32): W1, b1, ..., W6, b6 with W as
+ * [c_out][c_in][3][3]. */
+typedef struct mxp_cnn mxp_cnn;
+int64_t mxp_cnn_num_params(void);
+/* Buffers sized for batches up to max_batch of max_h x max_w images. */
+mxp_status mxp_cnn_create(int device, void *cuda_stream, int max_batch, int max_h, int max_w,
+                          mxp_cnn **out);
+/* Set the float32 master parameters (host array) and reset the Adam state. */
+mxp_status mxp_cnn_set_params(mxp_cnn *net, const float *host_params);
+mxp_status mxp_cnn_get_params(const mxp_cnn *net, float *host_params);
+/* y = network(x) for N images of H x W. */
+mxp_status mxp_cnn_forward(mxp_cnn *net, int N, int H, int W, const float *x_dev, float *y_dev);
+/* Parameter gradient of sum(gy * y) for the last forward (whose input was x_dev). */
+mxp_status mxp_cnn_backward(mxp_cnn *net, const float *x_dev, const float *gy_dev, float *grad_dev);
+/* One Adam step (lr, beta 0.9 / 0.999) on the mean squared error between the
+ * network output for x and target; *loss_out (nullable) receives the loss. */
+mxp_status mxp_cnn_train_step(mxp_cnn *net, int N, int H, int W, const float *x_dev,
+                              const float *target_dev, float lr, float *loss_out);
+void mxp_cnn_destroy(mxp_cnn *net);
+/* Use net as the first preconditioner of every FGMRES iteration of prob (2D):
+ * the direction z = net(v) is kept when the scaled residual
+ * min_a ||v - a A z|| / ||v|| <= accept_tol, otherwise MatExPre(v) is used.
+ * net = NULL detaches.  The network must accept the grid's n_y x n_x images. */
+mxp_status mxp_attach_cnn(mxp_problem *prob, mxp_cnn *net, double accept_tol);
 
 /* Number of unknowns prod_d n_d of the problem. */
 int64_t mxp_num_unknowns(const mxp_problem *prob);

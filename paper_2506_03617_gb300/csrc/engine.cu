@@ -131,6 +131,9 @@ struct mxp_problem {
     double *host_scal = nullptr;   // pinned, 8 doubles
     // counters
     int64_t passes = 0;
+    // learned stage
+    mxp_cnn *cnn = nullptr;
+    double cnn_tol = 0.5;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -905,7 +908,7 @@ static mxp_status fgmres_solve(mxp_problem *P, const double2 *b, double2 *x, con
         apply_op(P, 0, x, r);
         krylov_sub(r, b, r, n, st);
     }
-    int total = 0, inner_total = 0;
+    int total = 0, inner_total = 0, nn_acc = 0, nn_rej = 0;
     bool converged = false;
     double est = 0, relres = 1.0;
     mxp_status status = MXP_OK;
@@ -926,10 +929,30 @@ static mxp_status fgmres_solve(mxp_problem *P, const double2 *b, double2 *x, con
         if (total >= o->maxit) { status = MXP_ENOCONV; break; }
         int j = 0;
         for (; j < R && total < o->maxit; ++j) {
-            mxp_apply_stats ast{};
-            CKS(matexpre_apply(P, a.V + (size_t)j * n, a.Z + (size_t)j * n, &ast));
-            inner_total += ast.inner_iters;
-            apply_op(P, 0, a.Z + (size_t)j * n, a.V + (size_t)(j + 1) * n);
+            bool nn_used = false;
+            if (P->cnn && P->grid.dim == 2) {
+                // learned stage: z = net(v_j), kept if min_a ||v_j - a A z|| <= tol (||v_j|| = 1)
+                if (cnn_apply_vector(P->cnn, P->geom.n[0], P->geom.n[1], a.V + (size_t)j * n, 1.0,
+                                     P->c_dev, P->cmax, a.Z + (size_t)j * n) == MXP_OK) {
+                    apply_op(P, 0, a.Z + (size_t)j * n, a.V + (size_t)(j + 1) * n);
+                    krylov_mdot(a.V + (size_t)j * n, n, 1, a.V + (size_t)(j + 1) * n, n, a.tmpcol, 0, P->ks, st);
+                    krylov_nrm2sq(a.V + (size_t)(j + 1) * n, n, a.hs.scal + 5, P->ks, st);
+                    CK(cudaMemcpyAsync(P->host_scal + 1, a.tmpcol, sizeof(double2), cudaMemcpyDeviceToHost, st));
+                    CKS(read_scal(P, a.hs.scal + 5, 1));
+                    const double az2 = P->host_scal[0];
+                    const double dre = P->host_scal[1], dim_ = P->host_scal[2];
+                    const double rho2 = az2 > 0 ? 1.0 - (dre * dre + dim_ * dim_) / az2 : 1.0;
+                    const double rho = std::sqrt(std::max(0.0, rho2));
+                    nn_used = std::isfinite(rho) && rho <= P->cnn_tol;
+                    if (nn_used) ++nn_acc; else ++nn_rej;
+                }
+            }
+            if (!nn_used) {
+                mxp_apply_stats ast{};
+                CKS(matexpre_apply(P, a.V + (size_t)j * n, a.Z + (size_t)j * n, &ast));
+                inner_total += ast.inner_iters;
+                apply_op(P, 0, a.Z + (size_t)j * n, a.V + (size_t)(j + 1) * n);
+            }
             arnoldi_step(P, a, j);
             ++total;
             CK(cudaGetLastError());
@@ -959,6 +982,8 @@ static mxp_status fgmres_solve(mxp_problem *P, const double2 *b, double2 *x, con
         stats->stencil_passes = P->passes - passes0;
         stats->pt_updates = stats->stencil_passes * n;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats->nn_accepted = nn_acc;
+        stats->nn_rejected = nn_rej;
     }
     if (status == MXP_ENOCONV) return fail(MXP_ENOCONV, "outer FGMRES reached maxit");
     return MXP_OK;
@@ -1507,6 +1532,16 @@ mxp_status mxp_get_params(const mxp_problem *P, mxp_params *p)
 int64_t mxp_num_unknowns(const mxp_problem *P) { return P ? P->ntot : 0; }
 
 int mxp_num_tile_configs(void) { return fused2d_num_cfgs(); }
+
+mxp_status mxp_attach_cnn(mxp_problem *P, mxp_cnn *net, double accept_tol)
+{
+    if (!P) return fail(MXP_EINVAL, "NULL problem");
+    if (net && !(accept_tol >= 0 && accept_tol <= 1)) return fail(MXP_EINVAL, "accept_tol must lie in [0, 1]");
+    if (net && P->grid.dim != 2) return fail(MXP_EINVAL, "the learned stage is available for 2D problems");
+    P->cnn = net;
+    P->cnn_tol = accept_tol;
+    return MXP_OK;
+}
 
 int mxp_persist_config(const mxp_problem *P, int *ntiles)
 {

@@ -167,4 +167,8 @@ void hess_start(const HessState &hs, cudaStream_t st);
 // Solve the j x j upper-triangular system H y = g into hs.y.
 void hess_backsolve(const HessState &hs, int j, cudaStream_t st);
 
+// Learned stage: z = network(v) on a 2D grid (n0 x n1), see cnn.cu.
+mxp_status cnn_apply_vector(mxp_cnn *net, int n0, int n1, const double2 *v, double vnorm,
+                            const double *c, double cmax, double2 *z);
+
 }  // namespace mxp

@@ -194,3 +194,26 @@ def config_3d_lens(n_interior: int = 256, npml: int = 16):
     g = Grid(3, (n_interior,) * 3, npml)
     c = lens(g)
     return g, c, paper_params(g, c, ppw=10.0)
+
+
+# ---- learned preconditioning stage: seeded initial weights ----
+
+CNN_LAYERS = [  # (c_in, c_out, stride, upsample_input, relu), input order of the flat vector
+    (3, 32, 1, False, True),
+    (32, 64, 2, False, True),
+    (64, 64, 1, False, True),
+    (64, 64, 1, False, True),
+    (64, 32, 1, True, True),
+    (32, 2, 1, False, False),
+]
+
+
+def cnn_initial_params(seed: int) -> np.ndarray:
+    """He-normal initial weights (std sqrt(2 / fan_in)), zero biases, flat float32
+    vector in layer order W1, b1, ..., W6, b6 (W as [c_out][c_in][3][3])."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co, _, _, _ in CNN_LAYERS:
+        parts.append(rng.standard_normal(co * ci * 9) * math.sqrt(2.0 / (ci * 9)))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)

@@ -58,7 +58,8 @@ class SolveStats(ct.Structure):
     _fields_ = [("outer_iters", ct.c_int), ("inner_iters_total", ct.c_int),
                 ("converged", ct.c_int), ("true_relres", ct.c_double),
                 ("est_relres", ct.c_double), ("stencil_passes", ct.c_int64),
-                ("pt_updates", ct.c_int64), ("seconds", ct.c_double)]
+                ("pt_updates", ct.c_int64), ("seconds", ct.c_double),
+                ("nn_accepted", ct.c_int), ("nn_rejected", ct.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +90,18 @@ SIGNATURES = {
                                          ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
                                          ct.c_void_p, ct.POINTER(ct.c_int64)]),
     "mxp_num_unknowns": (ct.c_int64, [ct.c_void_p]),
+    "mxp_cnn_num_params": (ct.c_int64, []),
+    "mxp_cnn_create": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int,
+                                  ct.POINTER(ct.c_void_p)]),
+    "mxp_cnn_set_params": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_float)]),
+    "mxp_cnn_get_params": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_float)]),
+    "mxp_cnn_forward": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p,
+                                   ct.c_void_p]),
+    "mxp_cnn_backward": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "mxp_cnn_train_step": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p,
+                                      ct.c_void_p, ct.c_float, ct.POINTER(ct.c_float)]),
+    "mxp_cnn_destroy": (None, [ct.c_void_p]),
+    "mxp_attach_cnn": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_double]),
     "mxp_kernel_launch_count": (ct.c_int64, []),
     "mxp_num_tile_configs": (ct.c_int, []),
     "mxp_tile_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
@@ -263,6 +276,74 @@ class Problem:
                                         ct.c_void_p(x_host.ctypes.data), ct.byref(o),
                                         ct.byref(st)))
         return st.as_dict()
+
+
+class Cnn:
+    """The learned-stage network on one GPU (see include/matexpre.h)."""
+
+    def __init__(self, max_batch, max_h, max_w, device=0, stream=None):
+        import torch
+        self._lib = load()
+        self.device = int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ct.c_void_p()
+        _check(self._lib.mxp_cnn_create(self.device, _stream_handle(self.stream), int(max_batch),
+                                        int(max_h), int(max_w), ct.byref(h)))
+        self._h = h
+        self.num_params = int(self._lib.mxp_cnn_num_params())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mxp_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _fptr(t):
+        import torch
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError("tensors must be contiguous float32 CUDA tensors")
+        return ct.c_void_p(t.data_ptr())
+
+    def set_params(self, theta: np.ndarray):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        assert theta.size == self.num_params
+        _check(self._lib.mxp_cnn_set_params(self._h, theta.ctypes.data_as(ct.POINTER(ct.c_float))))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(self._lib.mxp_cnn_get_params(self._h, out.ctypes.data_as(ct.POINTER(ct.c_float))))
+        return out
+
+    def forward(self, x):
+        import torch
+        n, c, h, w = x.shape
+        y = torch.empty((n, 2, h, w), dtype=torch.float32, device=x.device)
+        _check(self._lib.mxp_cnn_forward(self._h, n, h, w, self._fptr(x), self._fptr(y)))
+        return y
+
+    def backward(self, x, gy):
+        import torch
+        g = torch.empty(self.num_params, dtype=torch.float32, device=x.device)
+        _check(self._lib.mxp_cnn_backward(self._h, self._fptr(x), self._fptr(gy), self._fptr(g)))
+        return g
+
+    def train_step(self, x, target, lr):
+        n, c, h, w = x.shape
+        loss = ct.c_float(0)
+        _check(self._lib.mxp_cnn_train_step(self._h, n, h, w, self._fptr(x), self._fptr(target),
+                                            float(lr), ct.byref(loss)))
+        return float(loss.value)
+
+
+def attach_cnn(problem, net, accept_tol=0.5):
+    _check(load().mxp_attach_cnn(problem._h, net._h if net is not None else None,
+                                 float(accept_tol)))
 
 
 def kernel_launch_count() -> int:
