@@ -38,6 +38,12 @@ UNIT = "Gpts/s"
 L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes per unknown of one exp-action Horner sweep: read p, y, kappa; write p
 BYTES_PER_PT = {"c128": 16 + 16 + 8 + 16, "c64": 8 + 8 + 4 + 8, "bf16s": 4 + 4 + 4 + 4}
+# float32 operations per point update of the fused / persistent sweeps (general PML
+# path): 4 complex multiply-adds for the neighbours (30), the diagonal (6), its
+# product with the centre (8), y + i tau q (4)
+FLOPS_PER_PT = 48
+# FP32 pipe peak of a GB300: 152 SMs x 128 lanes x 2 flops (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def parse_args():
@@ -58,8 +64,8 @@ def parse_args():
 
 
 def dist_env():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
-            int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2506_03617_gb300 import dist as D
+    return D.env()
 
 
 def workload():
@@ -186,9 +192,12 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- ours
 
-def kernel_hash():
+KERNEL_SOURCES = {"horner_step": "stencil.cu", "fused2d": "fused2d.cu", "persist2d": "persist2d.cu"}
+
+
+def kernel_hash(kernel):
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2506_03617_gb300", "csrc", "stencil.cu"), "rb") as fh:
+    with open(os.path.join(ROOT, "paper_2506_03617_gb300", "csrc", KERNEL_SOURCES[kernel]), "rb") as fh:
         h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -210,7 +219,7 @@ def recorded_traffic(kernel, prec):
         with open(path) as fh:
             rec = json.load(fh)
         e = rec.get(f"{kernel}:{prec}")
-        if e and e.get("kernel_sha") == kernel_hash():
+        if e and e.get("kernel_sha") == kernel_hash(kernel):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -266,14 +275,8 @@ def run_ours(args):
     launches = N.kernel_launch_count() - launches0
     clocks = sampler.stop()
     total = sum(times)
-    if world > 1:
-        t = torch.tensor([total, float(pts)], dtype=torch.float64, device=f"cuda:{dev}")
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_max, pts_all = float(tmax[0]), float(t[1])
-    else:
-        total_max, pts_all = total, float(pts)
+    from paper_2506_03617_gb300 import dist as D
+    total_max, pts_all = D.reduce_job(total, float(pts), device=f"cuda:{dev}")
     value = pts_all / total_max / 1e9
 
     if args.solve_only:
@@ -300,9 +303,12 @@ def run_ours(args):
            "d2h_bytes_per_step": 16 * n,
            "note": "mxp_solve_host: pinned host b -> device, solve, device x -> pinned host"}
 
-    # ---- roofline of the dominant kernel (Taylor-Horner sweep of the exp action)
+    # ---- roofline of the dominant kernel: the exp-action sweeps (>= 90% of the
+    # solve's sweeps); timed live here with CUDA events on the solve stream
     xr = torch.from_numpy(np.random.default_rng(3).standard_normal(n) + 0j).to(f"cuda:{dev}")
     yr = prob.empty()
+    pcfg, ptiles = prob.persist_config()
+    tcfg, tk = prob.tile_config()
     with torch.cuda.stream(stream):
         prob.apply_phi(0, xr, out=yr)
         torch.cuda.synchronize()
@@ -314,17 +320,33 @@ def run_ours(args):
             passes += prob.apply_phi(0, xr, out=yr)[1]
         ev1.record(stream)
         ev1.synchronize()
-    sweep_s = ev0.elapsed_time(ev1) / 1e3 / passes
+    t_act = ev0.elapsed_time(ev1) / 1e3 / reps
+    passes //= reps
     peak, peak_kind = measured_peak()
-    bytes_launch = BYTES_PER_PT[args.prec] * n
-    achieved = bytes_launch / sweep_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": recorded_traffic("horner_step", args.prec),
-                "kernel": f"k_step<{args.prec}> (one Taylor-Horner sweep of the exp action)",
-                "bytes_per_launch": bytes_launch, "launch_us": sweep_s * 1e6,
-                "peak_kind": f"{peak_kind} (copy bandwidth)",
-                "note": "1088^2 vectors are L2-resident (129 MB L2); the 3D 288^3 line "
-                        "below is the HBM-resident case"}
+    if pcfg >= 0 or tcfg >= 0:
+        # persistent (one launch per action) or fused (K steps per launch) sweeps
+        # keep the 1088^2 vectors on chip / in L2: bound by the SM, not by HBM
+        launches = 1 if pcfg >= 0 else max(1, passes // max(tk, 1))
+        flops_launch = FLOPS_PER_PT * n * passes / launches
+        achieved = flops_launch / (t_act / launches) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                    "traffic": recorded_traffic("persist2d" if pcfg >= 0 else "fused2d", args.prec),
+                    "kernel": (f"k_persist2d cfg {pcfg} ({ptiles} tiles, one launch per exp action)"
+                               if pcfg >= 0 else f"k_fused2d cfg {tcfg} (K={tk} steps per launch)"),
+                    "flops_per_launch": flops_launch, "launch_us": t_act / launches * 1e6,
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                    "hbm_equivalent_gbs": BYTES_PER_PT[args.prec] * n * passes / t_act / 1e9,
+                    "note": "per-sweep unfused bytes / time; the 1088^2 working set is L2/SM "
+                            "resident, so the HBM roofline applies to the 3D line"}
+    else:
+        bytes_launch = BYTES_PER_PT[args.prec] * n
+        achieved = bytes_launch / (t_act / passes) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": recorded_traffic("horner_step", args.prec),
+                    "kernel": f"k_step<{args.prec}> (one Taylor-Horner sweep)",
+                    "bytes_per_launch": bytes_launch, "launch_us": t_act / passes * 1e6,
+                    "peak_kind": f"{peak_kind} (copy bandwidth)"}
 
     extra = {}
     if world == 1 and rank == 0:
@@ -354,14 +376,44 @@ def run_ours(args):
             "frac": a3 / peak}
         del P3, x3, y3
         torch.cuda.empty_cache()
+        # many sources per medium in lockstep (one sweep launch per pass for the batch)
+        gb_ = I.Grid(2, (512, 512), 16)
+        cb_ = I.layered_grf(gb_, I.SEED_BASE + 3000 + 512)
+        pb_ = I.paper_params(gb_, cb_, ppw=8.0)
+        PB = N.Problem.from_grid(gb_, cb_, pb_, device=dev)
+        PB.set_params(prec=args.prec, exp_tol=1e-12 if args.prec == "c128" else 1e-6)
+        bsrc = [torch.from_numpy(I.rhs_from_source(I.gaussian_source(gb_, center=ctr)).ravel())
+                .to(f"cuda:{dev}") for ctr in I.random_centers(gb_, 8, seed=I.SEED_BASE + 3612)]
+        xsb = [PB.empty() for _ in bsrc]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        seq_pts = sum(PB.solve(bb, xx, rtol=rtol, maxit=300)[1]["pt_updates"] for bb, xx in zip(bsrc, xsb))
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        N.solve_batch([PB], [0] * 8, bsrc, xsb, rtol=rtol, maxit=300)     # captures graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bst = N.solve_batch([PB], [0] * 8, bsrc, xsb, rtol=rtol, maxit=300)
+        torch.cuda.synchronize()
+        t_bat = time.perf_counter() - t0
+        extra["batched_sources"] = {
+            "workload": "8 seeded Gaussian sources on a 512^2 + 16-PML layered medium",
+            "sequential_s": t_seq, "batched_s": t_bat,
+            "sequential_gpts": seq_pts / t_seq / 1e9,
+            "batched_gpts": sum(q["pt_updates"] for q in bst) / t_bat / 1e9,
+            "all_converged": all(q["converged"] for q in bst),
+            "max_true_relres": max(q["true_relres"] for q in bst)}
+        del PB
         if not args.no_fp64_compare and args.prec != "c128":
             prob.set_params(prec="c128", exp_tol=1e-12)
             t0 = time.perf_counter()
             _, st64 = prob.solve(b, x, rtol=rtol, maxit=300)
-            extra["fp64_solve"] = {"seconds": time.perf_counter() - t0,
+            t64 = time.perf_counter() - t0
+            extra["fp64_solve"] = {"seconds": t64,
                                    "outer": st64["outer_iters"],
                                    "inner": st64["inner_iters_total"],
-                                   "true_relres": st64["true_relres"]}
+                                   "true_relres": st64["true_relres"],
+                                   "speedup_of_this_precision": t64 / (total_max / args.steps)}
             prob.set_params(prec=args.prec, exp_tol=1e-6)
 
     cpu = None
