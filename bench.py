@@ -326,15 +326,15 @@ def run_ours(args):
     if pcfg >= 0 or tcfg >= 0:
         # persistent (one launch per action) or fused (K steps per launch) sweeps
         # keep the 1088^2 vectors on chip / in L2: bound by the SM, not by HBM
-        launches = 1 if pcfg >= 0 else max(1, passes // max(tk, 1))
-        flops_launch = FLOPS_PER_PT * n * passes / launches
-        achieved = flops_launch / (t_act / launches) / 1e12
+        nlaunch = 1 if pcfg >= 0 else max(1, passes // max(tk, 1))
+        flops_launch = FLOPS_PER_PT * n * passes / nlaunch
+        achieved = flops_launch / (t_act / nlaunch) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                     "traffic": recorded_traffic("persist2d" if pcfg >= 0 else "fused2d", args.prec),
                     "kernel": (f"k_persist2d cfg {pcfg} ({ptiles} tiles, one launch per exp action)"
                                if pcfg >= 0 else f"k_fused2d cfg {tcfg} (K={tk} steps per launch)"),
-                    "flops_per_launch": flops_launch, "launch_us": t_act / launches * 1e6,
+                    "flops_per_launch": flops_launch, "launch_us": t_act / nlaunch * 1e6,
                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                     "hbm_equivalent_gbs": BYTES_PER_PT[args.prec] * n * passes / t_act / 1e9,
                     "note": "per-sweep unfused bytes / time; the 1088^2 working set is L2/SM "
