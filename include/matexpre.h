@@ -263,6 +263,13 @@ void mxp_cnn_destroy(mxp_cnn *net);
  * net = NULL detaches.  The network must accept the grid's n_y x n_x images. */
 mxp_status mxp_attach_cnn(mxp_problem *prob, mxp_cnn *net, double accept_tol);
 
+/* Failure-detection self-test (no counterpart in the paper): launches the
+ * bounded device-side wait used by the persistent kernel's grid barrier with an
+ * arrival that never happens; the wait gives up after a few thousand polls,
+ * sets the problem's error word and the call returns MXP_ETIMEOUT.  The
+ * problem stays usable afterwards. */
+mxp_status mxp_selftest_barrier_timeout(mxp_problem *prob);
+
 /* Number of unknowns prod_d n_d of the problem. */
 int64_t mxp_num_unknowns(const mxp_problem *prob);
 

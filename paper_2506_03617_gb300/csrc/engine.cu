@@ -1533,6 +1533,15 @@ int64_t mxp_num_unknowns(const mxp_problem *P) { return P ? P->ntot : 0; }
 
 int mxp_num_tile_configs(void) { return fused2d_num_cfgs(); }
 
+mxp_status mxp_selftest_barrier_timeout(mxp_problem *P)
+{
+    if (!P) return fail(MXP_EINVAL, "NULL problem");
+    DeviceGuard guard(P->device);
+    CKS(ensure_base(P));
+    CK(barrier_selftest(P->bar, P->stream));
+    return read_scal(P, nullptr, 0);   // MXP_ETIMEOUT when the wait ran out (and clears it)
+}
+
 mxp_status mxp_attach_cnn(mxp_problem *P, mxp_cnn *net, double accept_tol)
 {
     if (!P) return fail(MXP_EINVAL, "NULL problem");

@@ -115,6 +115,9 @@ cudaError_t launch_persist2d(int cfg, const Geom &g, int npml, const float2 *coe
                              int pass_per_sub, float2 rho, unsigned *bar, int txo, int tyo,
                              int ntx, int nty, const S *x, S *ex0, S *ex1, S *out, cudaStream_t st);
 
+// Runs the bounded grid barrier with an arrival count that is never reached.
+cudaError_t barrier_selftest(unsigned *bar, cudaStream_t st);
+
 template <typename S>
 void launch_convert_in(const double2 *x, S *out, int64_t n, cudaStream_t st);
 // out = x (mode 0) or out = base - x (mode 1), both complex128

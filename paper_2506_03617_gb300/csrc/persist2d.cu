@@ -33,7 +33,8 @@ struct PersistArgs {
 
 constexpr long long kBarrierSpinLimit = 1ll << 24;   // x >= 32 ns sleep: about a second
 
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks)
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks,
+                                             long long limit = kBarrierSpinLimit)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -50,7 +51,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks)
         } else {
             long long it = 0;
             while (*vgen == gen) {
-                if (++it > kBarrierSpinLimit || *verr != 0u) {
+                if (++it > limit || *verr != 0u) {
                     atomicExch(bar + 2, 1u);
                     ok = 0;
                     break;
@@ -351,6 +352,23 @@ cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef
     if (e != cudaSuccess) return e;
     count_launch();
     return cudaLaunchCooperativeKernel(fn, dim3(ntx * nty), dim3(c.BX * c.BG), args, smem, st);
+}
+
+// Self-test of the bounded grid barrier: the blocks wait for one more arrival
+// than there are blocks, so every wait runs out after `limit` polls, sets the
+// error word and returns.  Nothing here can wait forever.
+__global__ void k_barrier_selftest(unsigned *bar, unsigned expected, long long limit)
+{
+    grid_barrier(bar, expected, limit);
+}
+
+cudaError_t barrier_selftest(unsigned *bar, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_barrier_selftest<<<2, 32, 0, st>>>(bar, 3u, 20000);
+    return cudaGetLastError();
 }
 
 #define MXP_PINST(S)                                                                          \

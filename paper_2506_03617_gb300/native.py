@@ -102,6 +102,7 @@ SIGNATURES = {
                                       ct.c_void_p, ct.c_float, ct.POINTER(ct.c_float)]),
     "mxp_cnn_destroy": (None, [ct.c_void_p]),
     "mxp_attach_cnn": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_double]),
+    "mxp_selftest_barrier_timeout": (ct.c_int, [ct.c_void_p]),
     "mxp_kernel_launch_count": (ct.c_int64, []),
     "mxp_num_tile_configs": (ct.c_int, []),
     "mxp_tile_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
