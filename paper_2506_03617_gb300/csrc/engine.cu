@@ -106,6 +106,7 @@ struct mxp_problem {
     int fused_tyo = 0;         // output-tile height of the fused sweeps (0 = largest)
     double fused_cost = 1e30;  // estimated ms per exp action with the per-pass kernels
     int persist_cfg = -1;      // persistent exp-action kernel (2D), -1 = not used
+    int f3_cfg = -1, f3_lz = 64;   // fused 3D exp sweeps, -1 = unfused
     int p_txo = 0, p_tyo = 0, p_ntx = 0, p_nty = 0;
     float *tau_dev = nullptr;  // per-step tau / h^2 of the exp plan (persistent kernel)
     size_t tau_cap = 0;
@@ -270,6 +271,7 @@ static int effective_fuse(const mxp_problem *P)
 
 static int exp_fuse(const mxp_problem *P)
 {
+    if (P->grid.dim == 3) return P->f3_cfg >= 0 ? fused3d_cfg_k(P->f3_cfg) : 1;
     return P->persist_cfg >= 0 ? persist2d_cfg_k(P->persist_cfg) : effective_fuse(P);
 }
 
@@ -379,7 +381,8 @@ static mxp_status validate_params(const mxp_params *p)
     if (p->prec != MXP_C128 && p->prec != MXP_C64 && p->prec != MXP_BF16S) return fail(MXP_EINVAL, "unknown precision");
     if (!fin(p->theta_max) || p->theta_max < 0 || p->theta_max > 30) return fail(MXP_EINVAL, "theta_max must lie in [0, 30]");
     if (p->fuse_k < 0 || p->fuse_k > kMaxFuse) return fail(MXP_EINVAL, "fuse_k must lie in [0, 8]");
-    if (p->tile_cfg < -1 || p->tile_cfg >= fused2d_num_cfgs()) return fail(MXP_EINVAL, "tile_cfg out of range");
+    if (p->tile_cfg < -1 || p->tile_cfg >= std::max(fused2d_num_cfgs(), fused3d_num_cfgs()))
+        return fail(MXP_EINVAL, "tile_cfg out of range");
     if (p->persist_cfg < -2 || p->persist_cfg >= persist2d_num_cfgs()) return fail(MXP_EINVAL, "persist_cfg out of range");
     return MXP_OK;
 }
@@ -647,6 +650,76 @@ static mxp_status tune_persist(mxp_problem *P, double best_cost)
     return MXP_OK;
 }
 
+// Pick the 3D exp sweep: time a few passes of each fused z-marching
+// configuration (and segment length) and the unfused kernel; keep the one with
+// the smallest (sweeps per action) x (time per sweep).  fuse_k as in 2D.
+template <typename S>
+static mxp_status tune_fused3(mxp_problem *P)
+{
+    P->f3_cfg = -1;
+    if (P->grid.dim != 3 || P->prm.prec == MXP_C128 || P->prm.fuse_k == 1) return MXP_OK;
+    if (P->prm.tile_cfg >= 0) {
+        if (P->prm.tile_cfg >= fused3d_num_cfgs()) return fail(MXP_EINVAL, "tile_cfg out of range for 3D");
+        P->f3_cfg = P->prm.tile_cfg;
+        P->f3_lz = 64;
+        return MXP_OK;
+    }
+    CKS(ensure_base(P));
+    const int64_t n = P->ntot;
+    S *b0 = (S *)P->hb[0], *b1 = (S *)P->hb[1], *b2 = (S *)P->hb[2];
+    CK(cudaMemsetAsync(b0, 0, (size_t)n * sizeof(S), P->stream));
+    CK(cudaMemsetAsync(b1, 0, (size_t)n * sizeof(S), P->stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = -1;
+    int best_cfg = -1, best_lz = 64;
+    for (int cfg = -1; cfg < fused3d_num_cfgs(); ++cfg) {
+        const int K = cfg >= 0 ? fused3d_cfg_k(cfg) : 1;
+        if (P->prm.fuse_k > 1 && K != P->prm.fuse_k) continue;
+        const TaylorPlan pl = make_plan(P->nu, P->prm.exp_tol, theta_of(P), K);
+        for (int lz : {32, 64, 128}) {
+            if (cfg < 0 && lz != 32) continue;
+            FusedStep steps[kMaxFuse];
+            for (int s = 0; s < K; ++s) steps[s] = FusedStep{1e-9, 0, 0, 1, 0, 0};
+            const int passes = std::max(2, 8 / K);
+            float best_ms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, P->stream);
+                for (int i = 0; i < passes; ++i) {
+                    if (cfg >= 0) {
+                        launch_fused3d<S>(cfg, lz, P->geom, P->coef32, P->kappa32, steps,
+                                          make_float2(1.0f, (float)P->prm.shift_s), (i & 1) ? b2 : b1, b0,
+                                          (i & 1) ? b1 : b2, P->stream);
+                    } else {
+                        StepScalars<typename St<S>::C> sc;
+                        sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
+                        sc.mu = 0;
+                        sc.sigma = PrecData<S>::c(cd(0.0, 1e-9));
+                        sc.gamma = PrecData<S>::c(cd(0.0));
+                        sc.rho = PrecData<S>::c(cd(1.0));
+                        launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc,
+                                       (i & 1) ? b2 : b1, b0, nullptr, (i & 1) ? b1 : b2, P->stream);
+                    }
+                }
+                cudaEventRecord(e1, P->stream);
+                CK(cudaEventSynchronize(e1));
+                CK(cudaGetLastError());
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) best_ms = std::min(best_ms, ms);
+            }
+            const double cost = best_ms / (passes * (double)K) * pl.S * pl.m;
+            if (best < 0 || cost < best) { best = cost; best_cfg = cfg; best_lz = lz; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P->f3_cfg = best_cfg;
+    P->f3_lz = best_lz;
+    return MXP_OK;
+}
+
 template <typename S>
 static mxp_status retune_t(mxp_problem *P)
 {
@@ -681,6 +754,14 @@ static mxp_status retune_t(mxp_problem *P)
 static mxp_status retune(mxp_problem *P)
 {
     P->persist_cfg = -1;
+    P->f3_cfg = -1;
+    if (P->grid.dim == 3) {
+        if (P->prm.prec == MXP_C64) CKS(tune_fused3<float2>(P));
+        else if (P->prm.prec == MXP_BF16S) CKS(tune_fused3<__nv_bfloat162>(P));
+        P->fused_cfg = -1;
+        make_plans(P);
+        return MXP_OK;
+    }
     switch (P->prm.prec) {
     case MXP_C64: CKS(retune_t<float2>(P)); break;
     case MXP_BF16S: CKS(retune_t<__nv_bfloat162>(P)); break;
@@ -727,6 +808,30 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
         launch_convert_out<S>(b[1], out, x, out_mode, n, st);
         P->passes += (int64_t)Ssub * m;
         return (int64_t)Ssub * m;
+    }
+    if (which == 0 && P->grid.dim == 3 && P->f3_cfg >= 0 && sizeof(S) <= 8 &&
+        m % fused3d_cfg_k(P->f3_cfg) == 0) {
+        const int K3 = fused3d_cfg_k(P->f3_cfg);
+        for (int sub = 0; sub < Ssub; ++sub) {
+            int in = iy;
+            for (int k = m; k >= 1; k -= K3) {
+                FusedStep steps[kMaxFuse];
+                for (int s = 0; s < K3; ++s) {
+                    const int kk = k - s;
+                    steps[s] = FusedStep{t / ((double)Ssub * kk), 0.0, 0.0, final_rho.real(), final_rho.imag(),
+                                         (sub == Ssub - 1 && kk == 1) ? 1 : 0};
+                }
+                const int o = (in == iy) ? (iy + 1) % 3 : 3 - iy - in;
+                launch_fused3d<S>(P->f3_cfg, P->f3_lz, P->geom, P->coef32, P->kappa32, steps,
+                                  make_float2(1.0f, (float)P->prm.shift_s), b[in], b[iy], b[o], st);
+                in = o;
+                passes += K3;
+            }
+            iy = in;
+        }
+        launch_convert_out<S>(b[iy], out, x, out_mode, n, st);
+        P->passes += passes;
+        return passes;
     }
     const int cfg = (sizeof(S) <= 8) ? P->fused_cfg : -1;
     const int K = cfg >= 0 ? fused2d_cfg_k(cfg) : 1;
@@ -1481,6 +1586,9 @@ mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, vo
     P->geom.s2 = (int64_t)n[0] * n[1];
     P->geom.ntot = ntot;
     P->geom.nmax = std::max(n[0], std::max(n[1], n[2]));
+    P->geom.fast = 1;
+    P->geom.npml = grid->npml;
+    P->geom.ih2 = 1.0 / (grid->h * grid->h);
     P->ntot = ntot;
     P->cmin = cmin;
     P->cmax = cmax;
@@ -1562,6 +1670,10 @@ int mxp_persist_config(const mxp_problem *P, int *ntiles)
 int mxp_tile_config(const mxp_problem *P, int *fuse_k)
 {
     if (!P) return -1;
+    if (P->grid.dim == 3) {
+        if (fuse_k) *fuse_k = P->f3_cfg >= 0 ? fused3d_cfg_k(P->f3_cfg) : 1;
+        return P->f3_cfg;
+    }
     if (fuse_k) *fuse_k = effective_fuse(P);
     return P->fused_cfg;
 }

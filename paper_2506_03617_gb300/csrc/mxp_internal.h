@@ -64,6 +64,9 @@ struct Geom {
     int64_t s1, s2;    // strides of axes 1 and 2
     int64_t ntot;
     int nmax;          // max_d n[d]: row length of the coefficient table
+    int fast = 0;      // 1: unknowns outside the PML use the real interior coefficient ih2
+    int npml = 0;
+    double ih2 = 0;    // 1 / h^2
 };
 
 // Scalars of one Taylor-Horner step  out = rho * (y + sigma * (A_s - mu) p + gamma * v)
@@ -103,6 +106,13 @@ template <typename S>
 bool launch_fused2d(int cfg, int tyo, const Geom &g, int npml, const float2 *coef, const float *kappa,
                     const FusedStep *steps, const float2 zfac, float mu, float ih2,
                     const S *pin, const S *y, const S *v, S *pout, cudaStream_t st, int nb = 1);
+
+// Fused 3D sweeps (z-marching temporal blocking, exp actions): see fused3d.cu.
+int fused3d_num_cfgs();
+int fused3d_cfg_k(int cfg);
+template <typename S>
+bool launch_fused3d(int cfg, int lz, const Geom &g, const float2 *coef, const float *kappa,
+                    const FusedStep *steps, float2 zfac, const S *pin, const S *y, S *pout, cudaStream_t st);
 
 // Persistent exp action (2D, float storage types): see persist2d.cu.
 int persist2d_num_cfgs();

@@ -36,25 +36,34 @@ __global__ void __launch_bounds__(128) k_step(Geom g, const typename St<S>::C *_
     const C pc = St<S>::ld(pin, q);
     C acc = czero<C>();
     C wcs = czero<C>();
+    // outside the PML every neighbour coefficient is the real 1/h^2: add the
+    // neighbours and scale once instead of multiplying complex coefficients
+    const int p0 = g.npml;
+    const bool inner = g.fast && i >= p0 && i < g.n[0] - p0 && (DIM < 2 || (j >= p0 && j < g.n[1] - p0)) &&
+                       (DIM < 3 || (k >= p0 && k < g.n[2] - p0));
     {
         const C xp = (i + 1 < g.n[0]) ? St<S>::ld(pin, q + 1) : czero<C>();
         const C xm = (i > 0) ? St<S>::ld(pin, q - 1) : czero<C>();
-        acc = cadd(acc, cadd(cmul(coef[i], xp), cmul(coef[nm + i], xm)));
+        acc = inner ? cadd(xp, xm) : cadd(cmul(coef[i], xp), cmul(coef[nm + i], xm));
         wcs = cadd(wcs, coef[2 * nm + i]);
     }
     if (DIM >= 2) {
         const C *cf = coef + 3 * nm;
         const C xp = (j + 1 < g.n[1]) ? St<S>::ld(pin, q + g.s1) : czero<C>();
         const C xm = (j > 0) ? St<S>::ld(pin, q - g.s1) : czero<C>();
-        acc = cadd(acc, cadd(cmul(cf[j], xp), cmul(cf[nm + j], xm)));
+        acc = cadd(acc, inner ? cadd(xp, xm) : cadd(cmul(cf[j], xp), cmul(cf[nm + j], xm)));
         wcs = cadd(wcs, cf[2 * nm + j]);
     }
     if (DIM >= 3) {
         const C *cf = coef + 6 * nm;
         const C xp = (k + 1 < g.n[2]) ? St<S>::ld(pin, q + g.s2) : czero<C>();
         const C xm = (k > 0) ? St<S>::ld(pin, q - g.s2) : czero<C>();
-        acc = cadd(acc, cadd(cmul(cf[k], xp), cmul(cf[nm + k], xm)));
+        acc = cadd(acc, inner ? cadd(xp, xm) : cadd(cmul(cf[k], xp), cmul(cf[nm + k], xm)));
         wcs = cadd(wcs, cf[2 * nm + k]);
+    }
+    if (inner) {
+        const R s = (R)g.ih2;
+        acc = CT<C>::mk(acc.x * s, acc.y * s);
     }
     const R kp = kappa[q];
     // diagonal: kappa (1 + i s) - mu - sum_d wc_d
