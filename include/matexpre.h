@@ -88,7 +88,12 @@ typedef struct {
  *  persist_cfg  persistent exp-action kernel (2D, MXP_C64 / MXP_BF16S): one
  *             cooperative launch per exp action with the grid held on chip;
  *             -1 = used when the autotuner finds it faster, -2 = never,
- *             >= 0 = force that configuration when the grid fits the GPU */
+ *             >= 0 = force that configuration when the grid fits the GPU
+ *  precond    preconditioner of mxp_apply_matexpre and mxp_solve: 0 = Algorithm 1
+ *             (default); 1 = the truncated Neumann series of Sec. 3.2,
+ *             P_N r = (sum_{n=0}^{N} exp(i t A_s)^n) psi_1(i t A_s) r (constant -i t
+ *             dropped; a fixed linear map, no inner GMRES; Thm. 3.1)
+ *  neumann_n  N of P_N (>= 0) */
 typedef struct {
     double omega, c_pml, shift_s, t, fprtol, exp_tol;
     int inner_restart, inner_maxit, inner_fixed;
@@ -97,6 +102,8 @@ typedef struct {
     int fuse_k;
     int tile_cfg;
     int persist_cfg;
+    int precond;
+    int neumann_n;
 } mxp_params;
 
 /* Statistics of one MatExPre apply (Algorithm 1). */
@@ -167,7 +174,8 @@ mxp_status mxp_apply_operator(mxp_problem *prob, int shifted, const void *x_dev,
 mxp_status mxp_apply_phi(mxp_problem *prob, int which, const void *x_dev, void *y_dev,
                          int64_t *passes_out);
 
-/* w = MatExPre(r): Algorithm 1 with the problem's parameters.  st nullable.
+/* w = MatExPre(r): Algorithm 1 with the problem's parameters (or P_N r when
+ * params.precond = 1; st->inner_iters then reports N).  st nullable.
  * Returns MXP_OK also when the inner GMRES stopped at inner_maxit (st->converged
  * tells which); MXP_ENAN if a residual became non-finite. */
 mxp_status mxp_apply_matexpre(mxp_problem *prob, const void *r_dev, void *w_dev,

@@ -12,6 +12,7 @@ Pinned functions (the pins live in ``tests/test_oracle_*.py``):
                                           expm of the operator matrix, semigroup
   matexpre   Algorithm 1               -- converged apply = (i/t) A_s^{-1} r
   fgmres     outer FGMRES              -- converged solution = direct solve
+  neumann    P_N of Sec. 3.2           -- eigenvalues of P_N A (Thm. 3.1)
 """
 from __future__ import annotations
 
@@ -80,6 +81,8 @@ def _load():
             lib.orc_fgmres.restype = None
             lib.orc_gmres_plain.argtypes = [P, ct.c_int, cd, cd, ct.c_double, ct.c_int,
                                             ct.c_int]
+            lib.orc_neumann.argtypes = [P, ct.c_int, ct.c_int, cd, cd]
+            lib.orc_neumann.restype = ct.c_int64
             lib.orc_gmres_plain.restype = ct.c_int
             _lib = lib
     return _lib
@@ -180,6 +183,14 @@ class Problem:
                     inner=[inner_log[i] for i in range(min(it, log_cap))],
                     res_hist=res_log[:it].copy())
         return u, info
+
+    def neumann(self, r, nterms, shifted=True):
+        """w = (sum_{n=0}^{N} exp(i t A_s)^n) psi_1(i t A_s) r (P_N of Sec. 3.2 without -i t)."""
+        r = self._vec(r)
+        w = np.empty_like(r)
+        _load().orc_neumann(ct.byref(self._s), int(bool(shifted)), int(nterms), self._ptr(r),
+                            self._ptr(w))
+        return w
 
     def gmres_plain(self, b, shifted=False, rtol=1e-10, restart=30, maxit=10000):
         b = self._vec(b)

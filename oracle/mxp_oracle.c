@@ -19,6 +19,8 @@
  *                 (Eq. fixed-point), constant -i t dropped (Sec. 3.4).
  *   orc_fgmres    outer flexible GMRES with Algorithm 1 as right preconditioner
  *                 (Sec. 3.4; restart 30 as in Sec. 4).
+ *   orc_neumann   truncated Neumann preconditioner P_N of Sec. 3.2 (Thm. 3.1),
+ *                 without its constant -i t.
  *
  * Grid reading (the paper gives only the 1D operator): unknown j of axis d
  * sits at x_j = (j - npml + 1/2) h, j = 0 .. n_d - 1, n_d = N_d + 2 npml;
@@ -421,6 +423,27 @@ int orc_matexpre(const orc_problem *P, const cplx *r, cplx *w, double fprtol,
     free(rt);
     if (spmv_out) *spmv_out = ctx.spmv;
     return st.iters;
+}
+
+/*
+ * Truncated Neumann preconditioner of Sec. 3.2 without its constant -i t:
+ * w = (sum_{n=0}^{N} exp(i t A_s)^n) psi_1(i t A_s) r.
+ */
+int64_t orc_neumann(const orc_problem *P, int shifted, int nterms, const cplx *r, cplx *w)
+{
+    int64_t n = n_total(P);
+    cplx *z = malloc(n * sizeof(cplx));
+    cplx *tmp = malloc(n * sizeof(cplx));
+    int64_t spmv = orc_phi(P, 1, shifted, r, z);
+    memcpy(w, z, n * sizeof(cplx));
+    for (int k = 1; k <= nterms; ++k) {
+        spmv += orc_phi(P, 0, shifted, z, tmp);
+        memcpy(z, tmp, n * sizeof(cplx));
+        for (int64_t i = 0; i < n; ++i) w[i] += z[i];
+    }
+    free(z);
+    free(tmp);
+    return spmv;
 }
 
 /* ---------- outer FGMRES ---------- */

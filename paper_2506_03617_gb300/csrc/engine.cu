@@ -384,6 +384,8 @@ static mxp_status validate_params(const mxp_params *p)
     if (p->tile_cfg < -1 || p->tile_cfg >= std::max(fused2d_num_cfgs(), fused3d_num_cfgs()))
         return fail(MXP_EINVAL, "tile_cfg out of range");
     if (p->persist_cfg < -2 || p->persist_cfg >= persist2d_num_cfgs()) return fail(MXP_EINVAL, "persist_cfg out of range");
+    if (p->precond != 0 && p->precond != 1) return fail(MXP_EINVAL, "precond must be 0 (Algorithm 1) or 1 (P_N)");
+    if (p->neumann_n < 0 || p->neumann_n > 10000) return fail(MXP_EINVAL, "neumann_n must lie in [0, 10000]");
     return MXP_OK;
 }
 
@@ -988,6 +990,38 @@ static mxp_status matexpre_apply(mxp_problem *P, const double2 *r, double2 *w, m
     return MXP_OK;
 }
 
+// Truncated Neumann preconditioner P_N of Sec. 3.2 (constant -i t dropped):
+// w = (sum_{n=0}^{N} exp(i t A_s)^n) psi_1(i t A_s) r; a fixed linear map.
+static mxp_status neumann_apply(mxp_problem *P, const double2 *r, double2 *w, mxp_apply_stats *stats)
+{
+    CKS(ensure_base(P));
+    const int64_t n = P->ntot;
+    const int64_t passes0 = P->passes;
+    if (phi_dispatch(P, 1, r, w, 0) < 0) return MXP_ECUDA;
+    double2 *z = P->rt, *zn = P->tmp;
+    krylov_copy(z, w, n, P->stream);
+    for (int k = 1; k <= P->prm.neumann_n; ++k) {
+        if (phi_dispatch(P, 0, z, zn, 0) < 0) return MXP_ECUDA;
+        krylov_add(w, zn, n, P->stream);
+        std::swap(z, zn);
+    }
+    CK(cudaGetLastError());
+    CKS(read_scal(P, nullptr, 0));
+    if (stats) {
+        stats->inner_iters = P->prm.neumann_n;
+        stats->converged = 1;
+        stats->inner_relres = 0.0;
+        stats->stencil_passes = P->passes - passes0;
+        stats->pt_updates = stats->stencil_passes * n;
+    }
+    return MXP_OK;
+}
+
+static mxp_status precond_apply(mxp_problem *P, const double2 *r, double2 *w, mxp_apply_stats *stats)
+{
+    return P->prm.precond == 1 ? neumann_apply(P, r, w, stats) : matexpre_apply(P, r, w, stats);
+}
+
 // Outer FGMRES(restart), right-preconditioned by Algorithm 1 (Sec. 3.4).
 static mxp_status fgmres_solve(mxp_problem *P, const double2 *b, double2 *x, const mxp_solve_opts *o,
                                mxp_solve_stats *stats)
@@ -1054,7 +1088,7 @@ static mxp_status fgmres_solve(mxp_problem *P, const double2 *b, double2 *x, con
             }
             if (!nn_used) {
                 mxp_apply_stats ast{};
-                CKS(matexpre_apply(P, a.V + (size_t)j * n, a.Z + (size_t)j * n, &ast));
+                CKS(precond_apply(P, a.V + (size_t)j * n, a.Z + (size_t)j * n, &ast));
                 inner_total += ast.inner_iters;
                 apply_op(P, 0, a.Z + (size_t)j * n, a.V + (size_t)(j + 1) * n);
             }
@@ -1377,6 +1411,7 @@ static mxp_status batch_solve(mxp_problem *P, int nr, const double2 *const *b, d
                               const mxp_solve_opts *o, mxp_solve_stats *stats)
 {
     const auto t0 = std::chrono::steady_clock::now();
+    if (P->prm.precond != 0) return fail(MXP_EINVAL, "batched solves use Algorithm 1 (precond = 0)");
     CKS(ensure_base(P));
     const int R = o->restart;
     CKS(ensure_batch(P, nr, R, P->prm.inner_restart));
@@ -1544,6 +1579,8 @@ mxp_status mxp_default_params(const mxp_grid *grid, double c_min, double ppw, mx
     p->fuse_k = 0;
     p->tile_cfg = -1;
     p->persist_cfg = -1;
+    p->precond = 0;
+    p->neumann_n = 4;
     return MXP_OK;
 }
 
@@ -1707,7 +1744,7 @@ mxp_status mxp_apply_matexpre(mxp_problem *P, const void *r_dev, void *w_dev, mx
     if (!P || !r_dev || !w_dev) return fail(MXP_EINVAL, "NULL argument");
     if (r_dev == w_dev) return fail(MXP_EINVAL, "r and w must not alias");
     DeviceGuard guard(P->device);
-    return matexpre_apply(P, (const double2 *)r_dev, (double2 *)w_dev, st);
+    return precond_apply(P, (const double2 *)r_dev, (double2 *)w_dev, st);
 }
 
 static mxp_status check_opts(const mxp_solve_opts *o)

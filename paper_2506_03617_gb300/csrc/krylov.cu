@@ -185,6 +185,19 @@ void krylov_sub(double2 *out, const double2 *a, const double2 *b, int64_t n, cud
     k_sub<<<grid_for(n, 256), 256, 0, st>>>(out, a, b, n);
 }
 
+__global__ void k_add(double2 *out, const double2 *a, int64_t n)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        out[p] = cadd(out[p], a[p]);
+}
+
+void krylov_add(double2 *out, const double2 *a, int64_t n, cudaStream_t st)
+{
+    count_launch();
+    k_add<<<grid_for(n, 256), 256, 0, st>>>(out, a, n);
+}
+
 void krylov_copy(double2 *out, const double2 *a, int64_t n, cudaStream_t st)
 {
     cudaMemcpyAsync(out, a, n * sizeof(double2), cudaMemcpyDeviceToDevice, st);

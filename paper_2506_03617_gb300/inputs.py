@@ -121,6 +121,7 @@ def layered_grf(grid: Grid, seed: int, vmin: float = 1.5, vmax: float = 4.5,
     rng = np.random.default_rng(seed)
     nlayers = int(rng.integers(6, 11))
     depth_cells = grid.ni[-1]
+    nlayers = min(nlayers, depth_cells)          # tiny grids: at most one layer per cell
     cuts = np.sort(rng.choice(np.arange(1, depth_cells), size=nlayers - 1, replace=False))
     vel = np.sort(rng.uniform(vmin, vmax, size=nlayers))
     vel[0], vel[-1] = vmin, vmax

@@ -40,7 +40,8 @@ class Params(ct.Structure):
                 ("t", ct.c_double), ("fprtol", ct.c_double), ("exp_tol", ct.c_double),
                 ("inner_restart", ct.c_int), ("inner_maxit", ct.c_int),
                 ("inner_fixed", ct.c_int), ("prec", ct.c_int), ("theta_max", ct.c_double),
-                ("fuse_k", ct.c_int), ("tile_cfg", ct.c_int), ("persist_cfg", ct.c_int)]
+                ("fuse_k", ct.c_int), ("tile_cfg", ct.c_int), ("persist_cfg", ct.c_int),
+                ("precond", ct.c_int), ("neumann_n", ct.c_int)]
 
 
 class ApplyStats(ct.Structure):
