@@ -430,8 +430,9 @@ static mxp_status ensure_base(mxp_problem *P)
     }
     if (!P->host_scal) CK(cudaMallocHost(&P->host_scal, 8 * sizeof(double)));
     if (!P->bar) {
-        CK(cudaMalloc(&P->bar, 4 * sizeof(unsigned)));
-        CK(cudaMemsetAsync(P->bar, 0, 4 * sizeof(unsigned), P->stream));
+        // [0..3] grid-barrier words and error flag, [4..] per-tile pass epochs
+        CK(cudaMalloc(&P->bar, (4 + 4096) * sizeof(unsigned)));
+        CK(cudaMemsetAsync(P->bar, 0, (4 + 4096) * sizeof(unsigned), P->stream));
     }
     return MXP_OK;
 }

@@ -14,6 +14,8 @@
 // error flag and every CTA leaves the pass loop, so the kernel always ends.
 // Co-residency of all CTAs is guaranteed by the cooperative launch (the launch
 // fails instead of deadlocking when the grid does not fit).
+#include <algorithm>
+
 #include "mxp_internal.h"
 
 namespace mxp {
@@ -28,10 +30,11 @@ struct PersistArgs {
     const float *tau;            // per step: tau / h^2 (operator scaled by h^2), npass * K
     int npass, pass_per_sub;     // passes in total and per sub-step
     float2 rho;                  // applied at the very last step
-    unsigned *bar;               // [0] arrival count, [1] generation, [2] error flag
+    unsigned *bar;               // [0] arrival count, [1] generation, [2] error flag, [4..] tile epochs
 };
 
 constexpr long long kBarrierSpinLimit = 1ll << 24;   // x >= 32 ns sleep: about a second
+constexpr long long kNeighbourPollLimit = 1ll << 21;  // L2 polls (~0.5 us each): about a second
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks,
                                              long long limit = kBarrierSpinLimit)
@@ -64,6 +67,42 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks,
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Point-to-point pass synchronisation: after publishing its strips for pass p a
+// CTA posts epoch p + 1, then waits until each of its (up to eight) neighbour
+// tiles has posted at least p + 1.  A CTA is therefore at most one pass ahead of
+// any neighbour, which keeps the two exchange buffers safe.  Bounded polling:
+// on timeout the error word is set and the caller stops.
+__device__ __forceinline__ bool neighbour_sync(unsigned *bar, int bx, int by, int ntx, int nty,
+                                               unsigned epoch)
+{
+    __shared__ int s_ok2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *flags = bar + 4;
+        volatile unsigned *verr = bar + 2;
+        __threadfence();
+        atomicExch(bar + 4 + by * ntx + bx, epoch);
+        int ok = 1;
+        for (int dy = -1; dy <= 1 && ok; ++dy)
+            for (int dx = -1; dx <= 1 && ok; ++dx) {
+                const int nx = bx + dx, ny = by + dy;
+                if ((dx == 0 && dy == 0) || nx < 0 || ny < 0 || nx >= ntx || ny >= nty) continue;
+                long long it = 0;
+                while (flags[ny * ntx + nx] < epoch) {
+                    if (++it > kNeighbourPollLimit || *verr != 0u) {
+                        atomicExch(bar + 2, 1u);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        __threadfence();
+        s_ok2 = ok && (*verr == 0u);
+    }
+    __syncthreads();
+    return s_ok2 != 0;
 }
 
 template <typename S, int K, int BX, int BG, int R, int CH>
@@ -144,7 +183,6 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
     }
     __syncthreads();
 
-    const unsigned nblocks = gridDim.x;
     bool alive = true;
     for (int pass = 0; pass < a.npass && alive; ++pass) {
 #pragma unroll 1
@@ -176,12 +214,31 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
                     const int ry = r0 + c + j;
                     const float2 wpy = cy[3 * ry], wmy = cy[3 * ry + 1], wcy = cy[3 * ry + 2];
                     // scaled diagonal h^2 (kappa (1 + i s) - wc_x - wc_y); mu is folded in wc
-                    const float2 d = make_float2(fmaf(kk[j], zh.x, -(wcx.x + wcy.x)),
-                                                 fmaf(kk[j], zh.y, -(wcx.y + wcy.y)));
-                    float2 q = cadd(cadd(cmul(wpx, e[j]), cmul(wmx, w[j])),
-                                    cadd(cmul(wpy, dn[j]), cmul(wmy, up)));
-                    q = cadd(q, cmul(d, cen));
-                    o[j] = make_float2(yr[c + j].x - tau * q.y, yr[c + j].y + tau * q.x);
+                    const float dx = fmaf(kk[j], zh.x, -(wcx.x + wcy.x));
+                    const float dy = fmaf(kk[j], zh.y, -(wcx.y + wcy.y));
+                    // q = wpx e + wmx w + wpy dn + wmy up + d cen as one FMA chain per component
+                    const float2 e_ = e[j], w_ = w[j], n_ = dn[j];
+                    float qx = wpx.x * e_.x;
+                    qx = fmaf(-wpx.y, e_.y, qx);
+                    qx = fmaf(wmx.x, w_.x, qx);
+                    qx = fmaf(-wmx.y, w_.y, qx);
+                    qx = fmaf(wpy.x, n_.x, qx);
+                    qx = fmaf(-wpy.y, n_.y, qx);
+                    qx = fmaf(wmy.x, up.x, qx);
+                    qx = fmaf(-wmy.y, up.y, qx);
+                    qx = fmaf(dx, cen.x, qx);
+                    qx = fmaf(-dy, cen.y, qx);
+                    float qy = wpx.x * e_.y;
+                    qy = fmaf(wpx.y, e_.x, qy);
+                    qy = fmaf(wmx.x, w_.y, qy);
+                    qy = fmaf(wmx.y, w_.x, qy);
+                    qy = fmaf(wpy.x, n_.y, qy);
+                    qy = fmaf(wpy.y, n_.x, qy);
+                    qy = fmaf(wmy.x, up.y, qy);
+                    qy = fmaf(wmy.y, up.x, qy);
+                    qy = fmaf(dx, cen.y, qy);
+                    qy = fmaf(dy, cen.x, qy);
+                    o[j] = make_float2(fmaf(-tau, qy, yr[c + j].x), fmaf(tau, qx, yr[c + j].y));
                     if (last) o[j] = cmul(a.rho, o[j]);
                     up = cen;
                     cen = dn[j];
@@ -205,7 +262,7 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
                 St<S>::st(ex, q, b0[(ry + 1) * PX + tx + 1]);
             }
         }
-        alive = grid_barrier(a.bar, nblocks);
+        alive = neighbour_sync(a.bar, bx, by, a.ntx, a.nty, (unsigned)(pass + 1));
         if (!alive) break;
         const bool sub_end = ((pass + 1) % a.pass_per_sub) == 0;
         // ring refresh: issue every L2 load first (clamped addresses), then store
@@ -248,7 +305,8 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
 struct PCfg {
     int K, BX, BG, R;
 };
-static const PCfg kPCfgs[] = {{2, 128, 4, 18}, {4, 96, 4, 28}, {4, 128, 4, 20}};
+static const PCfg kPCfgs[] = {{2, 128, 4, 18}, {4, 96, 4, 28}, {4, 96, 8, 14}, {4, 96, 9, 12},
+                               {2, 128, 8, 10}};
 constexpr int kNumP = sizeof(kPCfgs) / sizeof(kPCfgs[0]);
 
 int persist2d_num_cfgs() { return kNumP; }
@@ -270,7 +328,9 @@ static void cfg_info(int id, void **fn, size_t *smem)
     switch (id) {
     case 0: *fn = kernel_ptr<S, 2, 128, 4, 18>(); *smem = smem_bytes<S, 2, 128, 4, 18>(); break;
     case 1: *fn = kernel_ptr<S, 4, 96, 4, 28>(); *smem = smem_bytes<S, 4, 96, 4, 28>(); break;
-    default: *fn = kernel_ptr<S, 4, 128, 4, 20>(); *smem = smem_bytes<S, 4, 128, 4, 20>(); break;
+    case 2: *fn = kernel_ptr<S, 4, 96, 8, 14>(); *smem = smem_bytes<S, 4, 96, 8, 14>(); break;
+    case 3: *fn = kernel_ptr<S, 4, 96, 9, 12>(); *smem = smem_bytes<S, 4, 96, 9, 12>(); break;
+    default: *fn = kernel_ptr<S, 2, 128, 8, 10>(); *smem = smem_bytes<S, 2, 128, 8, 10>(); break;
     }
 }
 
@@ -296,10 +356,11 @@ bool persist2d_plan(int id, int n0, int n1, int device, int *txo, int *tyo, int 
         return false;
     }
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-    const int slots = per_sm * nsm;
+    int slots = per_sm * nsm;
     const int txmax = c.BX - 2 * c.K, tymax = c.BG * c.R - 2 * c.K;
     const int ntx_min = (n0 + txmax - 1) / txmax, nty_min = (n1 + tymax - 1) / tymax;
     if (slots < 1 || ntx_min * nty_min > slots) return false;
+    slots = std::min(slots, 4096);   // per-tile epoch words available
     long best_area = -1;
     for (int tx_n = ntx_min; tx_n <= n0 && tx_n <= slots; ++tx_n) {
         const int ty_n_max = slots / tx_n;
@@ -348,7 +409,7 @@ cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef
     a.bar = bar;
     void *args[] = {&a, (void *)&x, (void *)&ex0, (void *)&ex1, (void *)&out};
     const PCfg c = kPCfgs[id];
-    cudaError_t e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(bar, 0, (4 + (size_t)ntx * nty) * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     count_launch();
     return cudaLaunchCooperativeKernel(fn, dim3(ntx * nty), dim3(c.BX * c.BG), args, smem, st);
