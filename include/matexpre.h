@@ -194,9 +194,15 @@ mxp_status mxp_solve_host(mxp_problem *prob, const void *b_host, void *x_host,
 
 /* Many right-hand sides over several problems in one call.  Right-hand side r
  * belongs to problem probs[prob_of_rhs[r]]; b_dev[r], x_dev[r] are its vectors
- * on that problem's device.  All problems must share one device and stream.
- * Sources of a problem are solved together: their stencil sweeps run as one
- * launch over the batch.  per_rhs (nullable) has nrhs entries. */
+ * on that problem's device.  The sources of one problem advance in lockstep:
+ * their outer FGMRES and inner GMRES iterations run side by side and every
+ * exp / psi_1 action of the active sources is one sweep launch per pass over
+ * the batch, replayed from a captured CUDA graph; converged sources leave the
+ * batch.  Different problems (grid sizes, media) are solved concurrently, one
+ * host thread each; their kernels overlap on the GPU when the problems were
+ * created on different streams.  Requires precond = 0; the inner GMRES stops
+ * after inner_restart iterations if fprtol is not met.  per_rhs (nullable) has
+ * nrhs entries.  Returns MXP_ENOCONV if some source reached maxit. */
 mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs,
                            const int *prob_of_rhs, const void *const *b_dev,
                            void *const *x_dev, const mxp_solve_opts *opts,
@@ -209,6 +215,16 @@ int mxp_num_tile_configs(void);
 int mxp_tile_config(const mxp_problem *prob, int *fuse_k);
 /* Persistent exp-action kernel in use (-1 = none) and its tile count. */
 int mxp_persist_config(const mxp_problem *prob, int *ntiles);
+
+/* Tile planner of the persistent exp-action kernel (host only, no device
+ * call; the paper has no counterpart).  Splits an n0 x n1 grid into at most
+ * `slots` tiles of at most txmax x tymax cells, minimising the region (tile
+ * plus a k-cell ring) per CTA, with every tile but the last of each row and
+ * column at least k cells wide, so that a tile's ring lies inside its eight
+ * neighbours.  Writes the tile extents and the tile counts per axis; returns 1,
+ * or 0 when no plan fits or an argument is invalid (outputs then unchanged). */
+int mxp_persist_tile_plan(int n0, int n1, int slots, int k, int txmax, int tymax,
+                          int *txo, int *tyo, int *ntx, int *nty);
 
 /* Allocation-free exp / psi_1 action.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory when they need an

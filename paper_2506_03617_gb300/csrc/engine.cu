@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -1796,26 +1797,50 @@ mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs, const
         if (prob_of_rhs[r] < 0 || prob_of_rhs[r] >= nprob || !probs[prob_of_rhs[r]] || !b_dev[r] || !x_dev[r] ||
             b_dev[r] == x_dev[r])
             return fail(MXP_EINVAL, "invalid right-hand side entry");
-    mxp_status worst = MXP_OK;
-    for (int pi = 0; pi < nprob; ++pi) {
-        std::vector<int> idx;
-        for (int r = 0; r < nrhs; ++r)
-            if (prob_of_rhs[r] == pi) idx.push_back(r);
-        if (idx.empty()) continue;
-        mxp_problem *P = probs[pi];
+    // group the right-hand sides by problem handle (the same handle may appear twice)
+    std::vector<mxp_problem *> handles;
+    std::vector<std::vector<int>> groups;
+    for (int r = 0; r < nrhs; ++r) {
+        mxp_problem *P = probs[prob_of_rhs[r]];
+        size_t gi = std::find(handles.begin(), handles.end(), P) - handles.begin();
+        if (gi == handles.size()) {
+            handles.push_back(P);
+            groups.emplace_back();
+        }
+        groups[gi].push_back(r);
+    }
+    const size_t ng = groups.size();
+    std::vector<mxp_status> status(ng, MXP_OK);
+    std::vector<std::string> message(ng);
+    std::vector<std::vector<mxp_solve_stats>> stats(ng);
+    auto run = [&](size_t gi) {
+        mxp_problem *P = handles[gi];
         DeviceGuard guard(P->device);
         std::vector<const double2 *> bs;
         std::vector<double2 *> xs;
-        for (int r : idx) {
+        for (int r : groups[gi]) {
             bs.push_back((const double2 *)b_dev[r]);
             xs.push_back((double2 *)x_dev[r]);
         }
-        std::vector<mxp_solve_stats> st(idx.size());
-        mxp_status e = batch_solve(P, (int)idx.size(), bs.data(), xs.data(), opts, st.data());
+        stats[gi].assign(groups[gi].size(), mxp_solve_stats{});
+        status[gi] = batch_solve(P, (int)groups[gi].size(), bs.data(), xs.data(), opts, stats[gi].data());
+        if (status[gi] != MXP_OK) message[gi] = g_last_error;
+    };
+    if (ng == 1) {
+        run(0);
+    } else {
+        // different problems (grids, media) run concurrently, one host thread each;
+        // their kernels overlap on the GPU when the problems use different streams
+        std::vector<std::thread> th;
+        for (size_t gi = 0; gi < ng; ++gi) th.emplace_back(run, gi);
+        for (auto &t : th) t.join();
+    }
+    mxp_status worst = MXP_OK;
+    for (size_t gi = 0; gi < ng; ++gi) {
         if (per_rhs)
-            for (size_t q = 0; q < idx.size(); ++q) per_rhs[idx[q]] = st[q];
-        if (e != MXP_OK && e != MXP_ENOCONV) return e;
-        if (e == MXP_ENOCONV) worst = e;
+            for (size_t q = 0; q < groups[gi].size(); ++q) per_rhs[groups[gi][q]] = stats[gi][q];
+        if (status[gi] != MXP_OK && status[gi] != MXP_ENOCONV) return fail(status[gi], message[gi]);
+        if (status[gi] == MXP_ENOCONV) worst = MXP_ENOCONV;
     }
     if (worst == MXP_ENOCONV) return fail(MXP_ENOCONV, "a right-hand side did not converge");
     return MXP_OK;

@@ -15,6 +15,8 @@
 // moves in by one cell per step, so after K steps the inner tile is exact.
 // Unknowns outside the grid are forced to zero (Dirichlet) at every step.
 // Tiles whose region avoids the PML use the real interior coefficients 1/h^2.
+#include <mutex>
+
 #include "mxp_internal.h"
 
 namespace mxp {
@@ -201,11 +203,13 @@ static void launch_one(int n0, int n1, int npml, int nmax, int tyo, int nb, cons
 {
     constexpr int RY = RT * G;
     const size_t smem = (size_t)(2 * (RY + 2) * (RX + 2) + 2 * RY) * sizeof(float2);
-    static bool configured = false;   // per template instance
-    if (!configured) {
-        cudaFuncSetAttribute(k_fused2d<S, K, RX, RT, G, HAS_V>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
+    // opt in to large dynamic shared memory once per device (per template instance)
+    static std::atomic<bool> configured[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !configured[dev].load()) {
+        cudaFuncSetAttribute(k_fused2d<S, K, RX, RT, G, HAS_V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured[dev].store(true);
     }
     // balance the x tiles: ceil(n0 / (RX-2K)) tiles of equal width
     const int ntx = (n0 + RX - 2 * K - 1) / (RX - 2 * K);

@@ -11,6 +11,8 @@
 // steps; x-y halo values become wrong by one cell per level and are never
 // written.  Unknowns outside the grid stay zero (Dirichlet); tiles use the real
 // interior coefficient 1/h^2 outside the PML.
+#include <mutex>
+
 #include "mxp_internal.h"
 
 namespace mxp {
@@ -144,10 +146,13 @@ static void launch3(const Geom &g, int lz, const float2 *coef, const float *kapp
 {
     constexpr int PL = (BX + 2) * (BY + 2);
     const size_t smem = (size_t)(K * 3 + K + 1) * PL * sizeof(float2) + (size_t)(K + 1) * BX * BY * sizeof(float);
-    static bool configured = false;
-    if (!configured) {
+    // opt in to large dynamic shared memory once per device (per template instance)
+    static std::atomic<bool> configured[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !configured[dev].load()) {
         cudaFuncSetAttribute(k_fused3d<S, K, BX, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
+        configured[dev].store(true);
     }
     dim3 grid((g.n[0] + BX - 2 * K - 1) / (BX - 2 * K), (g.n[1] + BY - 2 * K - 1) / (BY - 2 * K),
               (g.n[2] + lz - 1) / lz);

@@ -35,6 +35,7 @@ struct PersistArgs {
 
 constexpr long long kBarrierSpinLimit = 1ll << 24;   // x >= 32 ns sleep: about a second
 constexpr long long kNeighbourPollLimit = 1ll << 21;  // L2 polls (~0.5 us each): about a second
+constexpr int kMaxPersistTiles = 4096;               // tile epoch words after the barrier header
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks,
                                              long long limit = kBarrierSpinLimit)
@@ -334,10 +335,43 @@ static void cfg_info(int id, void **fn, size_t *smem)
     }
 }
 
-// Tile plan for configuration id on an n0 x n1 grid: the largest number of
-// tiles that fits the co-resident CTAs, each no larger than the register /
-// shared-memory region of the configuration.  Returns false if the grid does
-// not fit on this device.
+// Tile plan: the largest number of tiles (at most `slots`, the co-resident
+// CTAs) that minimises the region (tile plus K-cell ring) of one CTA, each tile
+// no larger than txmax x tymax.  Every tile but the last one of a row or column
+// is at least K cells wide on both axes, so the ring of a tile lies inside its
+// eight neighbours: the point-to-point pass synchronisation only waits for
+// those.  Returns false if no plan fits.
+bool plan_tiles(int n0, int n1, int slots, int K, int txmax, int tymax, int *txo, int *tyo, int *ntx,
+                int *nty)
+{
+    if (n0 < 1 || n1 < 1 || slots < 1 || K < 1 || txmax < 1 || tymax < 1) return false;
+    const int ntx_min = (n0 + txmax - 1) / txmax, nty_min = (n1 + tymax - 1) / tymax;
+    if ((long)ntx_min * nty_min > slots) return false;
+    slots = std::min(slots, kMaxPersistTiles);   // per-tile epoch words available
+    long best_area = -1;
+    for (int tx_n = ntx_min; tx_n <= n0 && tx_n <= slots; ++tx_n) {
+        const int a = (n0 + tx_n - 1) / tx_n;
+        if (a < K && tx_n > ntx_min) break;       // narrower tiles would need a wider exchange
+        const int ty_n_max = slots / tx_n;
+        if (ty_n_max < nty_min) break;
+        for (int ty_n = nty_min; ty_n <= ty_n_max && ty_n <= n1; ++ty_n) {
+            const int b = (n1 + ty_n - 1) / ty_n;
+            if (b < K && ty_n > nty_min) break;
+            const long area = (long)(a + 2 * K) * (b + 2 * K);   // region per CTA
+            if (best_area < 0 || area < best_area) {
+                best_area = area;
+                *txo = a;
+                *tyo = b;
+                *ntx = (n0 + a - 1) / a;
+                *nty = (n1 + b - 1) / b;
+            }
+        }
+    }
+    return best_area > 0;
+}
+
+// Tile plan for configuration id on an n0 x n1 grid on this device.  Returns
+// false if the grid does not fit on this device.
 template <typename S>
 bool persist2d_plan(int id, int n0, int n1, int device, int *txo, int *tyo, int *ntx, int *nty)
 {
@@ -356,28 +390,7 @@ bool persist2d_plan(int id, int n0, int n1, int device, int *txo, int *tyo, int 
         return false;
     }
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-    int slots = per_sm * nsm;
-    const int txmax = c.BX - 2 * c.K, tymax = c.BG * c.R - 2 * c.K;
-    const int ntx_min = (n0 + txmax - 1) / txmax, nty_min = (n1 + tymax - 1) / tymax;
-    if (slots < 1 || ntx_min * nty_min > slots) return false;
-    slots = std::min(slots, 4096);   // per-tile epoch words available
-    long best_area = -1;
-    for (int tx_n = ntx_min; tx_n <= n0 && tx_n <= slots; ++tx_n) {
-        const int ty_n_max = slots / tx_n;
-        if (ty_n_max < nty_min) break;
-        for (int ty_n = nty_min; ty_n <= ty_n_max && ty_n <= n1; ++ty_n) {
-            const int a = (n0 + tx_n - 1) / tx_n, b = (n1 + ty_n - 1) / ty_n;
-            const long area = (long)(a + 2 * c.K) * (b + 2 * c.K);   // region per CTA
-            if (best_area < 0 || area < best_area) {
-                best_area = area;
-                *txo = a;
-                *tyo = b;
-                *ntx = (n0 + a - 1) / a;
-                *nty = (n1 + b - 1) / b;
-            }
-        }
-    }
-    return best_area > 0;
+    return plan_tiles(n0, n1, per_sm * nsm, c.K, c.BX - 2 * c.K, c.BG * c.R - 2 * c.K, txo, tyo, ntx, nty);
 }
 
 template <typename S>
@@ -443,3 +456,10 @@ MXP_PINST(__nv_bfloat162)
 #undef MXP_PINST
 
 }  // namespace mxp
+
+extern "C" int mxp_persist_tile_plan(int n0, int n1, int slots, int k, int txmax, int tymax, int *txo, int *tyo,
+                                     int *ntx, int *nty)
+{
+    if (!txo || !tyo || !ntx || !nty) return 0;
+    return mxp::plan_tiles(n0, n1, slots, k, txmax, tymax, txo, tyo, ntx, nty) ? 1 : 0;
+}

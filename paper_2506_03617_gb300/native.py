@@ -108,6 +108,7 @@ SIGNATURES = {
     "mxp_num_tile_configs": (ct.c_int, []),
     "mxp_tile_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_persist_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
+    "mxp_persist_tile_plan": (ct.c_int, [ct.c_int] * 6 + [ct.POINTER(ct.c_int)] * 4),
     "mxp_destroy": (None, [ct.c_void_p]),
     "mxp_status_string": (ct.c_char_p, [ct.c_int]),
     "mxp_last_error": (ct.c_char_p, []),
@@ -346,6 +347,14 @@ class Cnn:
 def attach_cnn(problem, net, accept_tol=0.5):
     _check(load().mxp_attach_cnn(problem._h, net._h if net is not None else None,
                                  float(accept_tol)))
+
+
+def persist_tile_plan(n0, n1, slots, k, txmax, tymax):
+    """Tile plan of the persistent exp kernel: (txo, tyo, ntx, nty) or None."""
+    out = [ct.c_int(0) for _ in range(4)]
+    ok = load().mxp_persist_tile_plan(int(n0), int(n1), int(slots), int(k), int(txmax), int(tymax),
+                                      *[ct.byref(v) for v in out])
+    return tuple(int(v.value) for v in out) if ok else None
 
 
 def kernel_launch_count() -> int:

@@ -64,3 +64,39 @@ def test_batch_is_repeatable_with_replayed_graphs(native):
     native.solve_batch([G], [0] * 4, bs, x2)          # second call replays captured graphs
     for a, b in zip(x1, x2):
         assert torch.equal(a, b)
+
+
+def test_uneven_problems_solve_concurrently_on_their_own_streams(native):
+    """Problems of different grid sizes in one call run in their own host
+    threads; each uses the stream it was created on."""
+    grids = [I.Grid(2, (160, 144), 12), I.Grid(2, (72, 64), 8)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    probs, oracles, srcs = [], [], []
+    for k, (g, s) in enumerate(zip(grids, streams)):
+        c = I.layered_grf(g, seed=I.SEED_BASE + 4200 + k, corr_cells=4.0)
+        p = I.paper_params(g, c, ppw=10.0)
+        G = native.Problem.from_grid(g, c, p, stream=s)
+        G.set_params(prec="c64", exp_tol=1e-6)
+        probs.append(G)
+        oracles.append(oracle.Problem.from_grid(g, c, p))
+        for ctr in I.random_centers(g, 2, seed=I.SEED_BASE + 4300 + k):
+            srcs.append((k, I.rhs_from_source(I.gaussian_source(g, center=ctr)).ravel()))
+    srcs = [srcs[2], srcs[0], srcs[1], srcs[3]]       # right-hand sides interleaved across problems
+    bs = [torch.from_numpy(b).cuda() for _, b in srcs]
+    xs = [probs[k].empty() for k, _ in srcs]
+    torch.cuda.synchronize()
+    stats = native.solve_batch(probs, [k for k, _ in srcs], bs, xs, rtol=1e-6, maxit=100)
+    torch.cuda.synchronize()
+    for (k, b), x, st in zip(srcs, xs, stats):
+        assert st["converged"], st
+        xh = x.cpu().numpy()
+        assert np.linalg.norm(b - oracles[k].apply(xh)) / np.linalg.norm(b) <= 1.000001e-6
+    # each problem alone gives the same solutions to the solve tolerance
+    for k in range(2):
+        mine = [i for i, (kk, _) in enumerate(srcs) if kk == k]
+        xs1 = [probs[k].empty() for _ in mine]
+        native.solve_batch([probs[k]], [0] * len(mine), [bs[i] for i in mine], xs1, rtol=1e-6,
+                           maxit=100)
+        torch.cuda.synchronize()
+        for i, x1 in zip(mine, xs1):
+            assert _rel(xs[i].cpu().numpy(), x1.cpu().numpy()) < 1e-4
