@@ -13,6 +13,9 @@ Pinned functions (the pins live in ``tests/test_oracle_*.py``):
   matexpre   Algorithm 1               -- converged apply = (i/t) A_s^{-1} r
   fgmres     outer FGMRES              -- converged solution = direct solve
   neumann    P_N of Sec. 3.2           -- eigenvalues of P_N A (Thm. 3.1)
+  phi(2), matexpre(variant=1)         -- psi_2 scalar closed form, dense expm of
+             second inverse formula       the augmented matrix, converged apply =
+                                          (i/t) A_s^{-1} r
 """
 from __future__ import annotations
 
@@ -74,6 +77,14 @@ def _load():
             lib.orc_matexpre.argtypes = [P, cd, cd, ct.c_double, ct.c_int, ct.c_int,
                                          ct.c_int, ct.POINTER(ct.c_int64)]
             lib.orc_matexpre.restype = ct.c_int
+            lib.orc_matexpre_v.argtypes = [P, ct.c_int, cd, cd, ct.c_double, ct.c_int, ct.c_int,
+                                           ct.c_int, ct.POINTER(ct.c_int64)]
+            lib.orc_matexpre_v.restype = ct.c_int
+            lib.orc_fgmres_v.argtypes = [P, ct.c_int, cd, cd, ct.c_double, ct.c_int, ct.c_int,
+                                         ct.c_double, ct.c_int, ct.c_int, ct.c_int,
+                                         ct.POINTER(ct.c_int), ct.c_int, cd,
+                                         ct.POINTER(_SolveStats)]
+            lib.orc_fgmres_v.restype = None
             lib.orc_fgmres.argtypes = [P, cd, cd, ct.c_double, ct.c_int, ct.c_int,
                                        ct.c_double, ct.c_int, ct.c_int, ct.c_int,
                                        ct.POINTER(ct.c_int), ct.c_int, cd,
@@ -137,7 +148,8 @@ class Problem:
         return y
 
     def phi(self, which, x, shifted=True):
-        """which=0: exp(i t A_s) x; which=1: psi_1(i t A_s) x.  Returns (y, spmv)."""
+        """which=0: exp(i t A_s) x; 1: psi_1(i t A_s) x; 2: psi_2(i t A_s) x.
+        Returns (y, spmv)."""
         x = self._vec(x)
         y = np.empty_like(x)
         sp = _load().orc_phi(ct.byref(self._s), int(which), int(bool(shifted)),
@@ -153,30 +165,33 @@ class Problem:
     def norm_inf_tA(self, shifted=True):
         return float(_load().orc_norm_inf_tA(ct.byref(self._s), int(bool(shifted))))
 
-    def matexpre(self, r, fprtol=0.08, restart=30, maxit=1000, fixed=0):
-        """Algorithm 1.  Returns (w, inner_iterations, spmv)."""
+    def matexpre(self, r, fprtol=0.08, restart=30, maxit=1000, fixed=0, variant=0):
+        """Algorithm 1 (variant 0) or its form on the second inverse formula,
+        psi_2 right-hand side and I - psi_1 operator (variant 1).
+        Returns (w, inner_iterations, spmv)."""
         r = self._vec(r)
         w = np.empty_like(r)
         sp = ct.c_int64(0)
-        it = _load().orc_matexpre(ct.byref(self._s), self._ptr(r), self._ptr(w),
-                                  float(fprtol), int(restart), int(maxit), int(fixed),
-                                  ct.byref(sp))
+        it = _load().orc_matexpre_v(ct.byref(self._s), int(variant), self._ptr(r), self._ptr(w),
+                                    float(fprtol), int(restart), int(maxit), int(fixed),
+                                    ct.byref(sp))
         return w, int(it), int(sp.value)
 
     def fgmres(self, b, rtol=1e-6, restart=30, maxit=200, fprtol=0.08, inner_restart=30,
-               inner_maxit=1000, inner_fixed=0, x0=None):
-        """Outer FGMRES with Algorithm 1 as right preconditioner.
-        Returns (u, info dict)."""
+               inner_maxit=1000, inner_fixed=0, x0=None, variant=0):
+        """Outer FGMRES with Algorithm 1 (or its variant, see matexpre) as right
+        preconditioner.  Returns (u, info dict)."""
         b = self._vec(b)
         u = np.zeros_like(b) if x0 is None else self._vec(x0).copy()
         log_cap = 4096
         inner_log = (ct.c_int * log_cap)()
         res_log = np.zeros(max(maxit, 1), dtype=np.float64)
         st = _SolveStats()
-        _load().orc_fgmres(ct.byref(self._s), self._ptr(b), self._ptr(u), float(rtol),
-                           int(restart), int(maxit), float(fprtol), int(inner_restart),
-                           int(inner_maxit), int(inner_fixed), inner_log, log_cap,
-                           res_log.ctypes.data_as(ct.POINTER(ct.c_double)), ct.byref(st))
+        _load().orc_fgmres_v(ct.byref(self._s), int(variant), self._ptr(b), self._ptr(u),
+                             float(rtol), int(restart), int(maxit), float(fprtol),
+                             int(inner_restart), int(inner_maxit), int(inner_fixed), inner_log,
+                             log_cap, res_log.ctypes.data_as(ct.POINTER(ct.c_double)),
+                             ct.byref(st))
         it = st.outer_iters
         info = dict(outer_iters=it, converged=bool(st.converged),
                     true_relres=st.true_relres, est_relres=st.est_relres, spmv=int(st.spmv),

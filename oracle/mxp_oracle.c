@@ -12,8 +12,8 @@
  *                 shift (Eq. helmholtz; Eq. pml-1d-s, extended to 2D/3D by
  *                 stretching each axis; shifted operator A_s = A + i w^2 s D of
  *                 Sec. 3.4 "Numerical strategies").
- *   orc_phi       exp(M)v and psi_1(M)v for M = i t A_s (Def. psi): truncated
- *                 Taylor series over sub-steps.
+ *   orc_phi       exp(M)v, psi_1(M)v and psi_2(M)v for M = i t A_s (Def. psi):
+ *                 truncated Taylor series over sub-steps.
  *   orc_matexpre  Algorithm 1: r <- psi_1(i t A_s) r, then GMRES on
  *                 (I - exp(i t A_s)) w = r to relative tolerance fprtol
  *                 (Eq. fixed-point), constant -i t dropped (Sec. 3.4).
@@ -21,6 +21,9 @@
  *                 (Sec. 3.4; restart 30 as in Sec. 4).
  *   orc_neumann   truncated Neumann preconditioner P_N of Sec. 3.2 (Thm. 3.1),
  *                 without its constant -i t.
+ *   orc_matexpre_v  Algorithm 1 (variant 0) or the same steps on the second
+ *                 inverse formula of Sec. 3.1 (variant 1): r <- psi_2(i t A_s) r,
+ *                 GMRES on (I - psi_1(i t A_s)) w = r.
  *
  * Grid reading (the paper gives only the 1D operator): unknown j of axis d
  * sits at x_j = (j - npml + 1/2) h, j = 0 .. n_d - 1, n_d = N_d + 2 npml;
@@ -210,13 +213,21 @@ double orc_norm_inf_tA(const orc_problem *P, int shifted)
 /* ---------- matrix functions (Def. psi) ---------- */
 
 /*
- * which = 0: y = exp(M) x;  which = 1: y = psi_1(M) x;  M = i t A_s (or i t A).
+ * which = 0: y = exp(M) x;  which = 1: y = psi_1(M) x;  which = 2: y = psi_2(M) x;
+ * M = i t A_s (or i t A).
  *
- * Sub-stepping: with X = M / m_sub, the solution of u' = M u + g on [0, 1]
- * advances over one sub-step of length 1/m_sub as
- *     u <- exp(X) u + (1/m_sub) psi_1(X) g,
- * and exp(X) z = sum_k X^k z / k!, psi_1(X) z = sum_k X^k z / (k+1)!.
- * exp(M)x is u(1) for u(0) = x, g = 0; psi_1(M)x is u(1) for u(0) = 0, g = x.
+ * The psi functions are solutions of linear ODEs on [0, 1] (Def. psi, through
+ * psi_l(z) = int_0^1 exp((1 - s) z) s^(l-1) / (l-1)! ds):
+ *   exp(M)x   = u(1) for u' = M u,          u(0) = x;
+ *   psi_1(M)x = u(1) for u' = M u + x,      u(0) = 0;
+ *   psi_2(M)x = u(1) for u' = M u + tau x,  u(0) = 0.
+ * Sub-stepping with step length hs = 1/m_sub and X = hs M: by variation of
+ * constants, over the sub-step starting at tau_j = j hs
+ *   u <- exp(X) u + hs psi_1(X) g_j + hs^2 psi_2(X) g',
+ * where g_j is the forcing at tau_j (x for psi_1, tau_j x for psi_2) and g' its
+ * slope (0 for psi_1, x for psi_2).  Each function is its Taylor series:
+ * exp(X) z = sum_k X^k z / k!, psi_1(X) z = sum_k X^k z / (k+1)!,
+ * psi_2(X) z = sum_k X^k z / (k+2)!.
  * m_sub = ceil(||M||_inf / 2), so ||X|| <= 2 and the Taylor terms shrink at
  * least geometrically once k >= 2; summation stops when the newest terms fall
  * below 1e-17 of the partial sum.
@@ -232,39 +243,51 @@ int64_t orc_phi(const orc_problem *P, int which, int shifted, const cplx *x, cpl
     int64_t spmv = 0;
 
     cplx *u = calloc(n, sizeof(cplx));
-    cplx *ta = malloc(n * sizeof(cplx));   /* X^k u / k!           */
-    cplx *tb = malloc(n * sizeof(cplx));   /* X^k g / (m_sub (k+1)!) */
+    cplx *ta = malloc(n * sizeof(cplx));   /* X^k u / k!                   */
+    cplx *tb = malloc(n * sizeof(cplx));   /* hs X^k g_j / (k+1)!          */
+    cplx *tc = malloc(n * sizeof(cplx));   /* hs^2 X^k g' / (k+2)!         */
     cplx *tmp = malloc(n * sizeof(cplx));
     cplx *next = malloc(n * sizeof(cplx));
-    const cplx *g = (which == 1) ? x : NULL;
+    const int has_b = (which >= 1), has_c = (which == 2);
     if (which == 0) memcpy(u, x, n * sizeof(cplx));
 
     for (int step = 0; step < m_sub; ++step) {
+        /* forcing at the sub-step start: x (psi_1) or tau_j x (psi_2) */
+        double gj = (which == 1) ? 1.0 : (double)step * inv_m;
         /* k = 0 terms */
         memcpy(ta, u, n * sizeof(cplx));
-        if (g) for (int64_t i = 0; i < n; ++i) tb[i] = g[i] * inv_m;
+        for (int64_t i = 0; i < n; ++i) {
+            tb[i] = has_b ? x[i] * (gj * inv_m) : 0.0;
+            tc[i] = has_c ? x[i] * (inv_m * inv_m / 2.0) : 0.0;
+        }
         cplx *acc = tmp;
-        for (int64_t i = 0; i < n; ++i) acc[i] = ta[i] + (g ? tb[i] : 0.0);
+        for (int64_t i = 0; i < n; ++i) acc[i] = ta[i] + tb[i] + tc[i];
         for (int k = 1; k < 400; ++k) {
             /* ta <- X ta / k */
             orc_apply(P, shifted, ta, next); ++spmv;
             for (int64_t i = 0; i < n; ++i) ta[i] = xfac * next[i] / (double)k;
-            double na = vnorm(n, ta), nb = 0.0;
-            if (g) {
+            double na = vnorm(n, ta), nb = 0.0, nc = 0.0;
+            if (has_b) {
                 /* tb <- X tb / (k+1) */
                 orc_apply(P, shifted, tb, next); ++spmv;
                 for (int64_t i = 0; i < n; ++i) tb[i] = xfac * next[i] / (double)(k + 1);
                 nb = vnorm(n, tb);
             }
-            for (int64_t i = 0; i < n; ++i) acc[i] += ta[i] + (g ? tb[i] : 0.0);
+            if (has_c) {
+                /* tc <- X tc / (k+2) */
+                orc_apply(P, shifted, tc, next); ++spmv;
+                for (int64_t i = 0; i < n; ++i) tc[i] = xfac * next[i] / (double)(k + 2);
+                nc = vnorm(n, tc);
+            }
+            for (int64_t i = 0; i < n; ++i) acc[i] += ta[i] + tb[i] + tc[i];
             double ns = vnorm(n, acc);
-            if (k >= 3 && na + nb <= 1e-17 * ns) break;
-            if (ns == 0.0 && na + nb == 0.0) break;
+            if (k >= 3 && na + nb + nc <= 1e-17 * ns) break;
+            if (ns == 0.0 && na + nb + nc == 0.0) break;
         }
         memcpy(u, acc, n * sizeof(cplx));
     }
     memcpy(y, u, n * sizeof(cplx));
-    free(u); free(ta); free(tb); free(tmp); free(next);
+    free(u); free(ta); free(tb); free(tc); free(tmp); free(next);
     return spmv;
 }
 
@@ -390,31 +413,35 @@ done:
 
 typedef struct {
     const orc_problem *P;
+    int which;          /* 0: exp (Algorithm 1), 1: psi_1 (second inverse formula) */
     int64_t spmv;
 } fp_ctx;
 
-/* out = (I - exp(i t A_s)) in  (Eq. fixed-point) */
+/* out = (I - phi(i t A_s)) in, phi = exp (Eq. fixed-point) or psi_1 */
 static void fixed_point_op(void *vctx, const cplx *in, cplx *out)
 {
     fp_ctx *c = vctx;
     int64_t n = n_total(c->P);
-    c->spmv += orc_phi(c->P, 0, 1, in, out);
+    c->spmv += orc_phi(c->P, c->which, 1, in, out);
     for (int64_t i = 0; i < n; ++i) out[i] = in[i] - out[i];
 }
 
 /*
- * Algorithm 1: r <- psi_1(i t A_s) r; zeta = ||r||; GMRES(restart), x0 = 0, on
- * (I - exp(i t A_s)) w = r until the residual estimate is <= fprtol * zeta (or
- * exactly `fixed` iterations when fixed > 0, or maxit iterations).
+ * variant 0, Algorithm 1: r <- psi_1(i t A_s) r; zeta = ||r||; GMRES(restart),
+ * x0 = 0, on (I - exp(i t A_s)) w = r until the residual estimate is
+ * <= fprtol * zeta (or exactly `fixed` iterations when fixed > 0, or maxit).
+ * variant 1, the same steps on the second inverse formula of Sec. 3.1,
+ * A^{-1} = -i t (I - psi_1(i t A))^{-1} psi_2(i t A): r <- psi_2(i t A_s) r and
+ * GMRES on (I - psi_1(i t A_s)) w = r.  Both give w ~ (i/t) A_s^{-1} r.
  * Returns the number of inner iterations; *spmv_out gets the operator count.
  */
-int orc_matexpre(const orc_problem *P, const cplx *r, cplx *w, double fprtol,
-                 int restart, int maxit, int fixed, int64_t *spmv_out)
+int orc_matexpre_v(const orc_problem *P, int variant, const cplx *r, cplx *w, double fprtol,
+                   int restart, int maxit, int fixed, int64_t *spmv_out)
 {
     int64_t n = n_total(P);
     cplx *rt = malloc(n * sizeof(cplx));
-    fp_ctx ctx = {P, 0};
-    ctx.spmv += orc_phi(P, 1, 1, r, rt);
+    fp_ctx ctx = {P, variant == 1 ? 1 : 0, 0};
+    ctx.spmv += orc_phi(P, variant == 1 ? 2 : 1, 1, r, rt);
     double zeta = vnorm(n, rt);
     memset(w, 0, n * sizeof(cplx));
     orc_krylov_stats st;
@@ -423,6 +450,12 @@ int orc_matexpre(const orc_problem *P, const cplx *r, cplx *w, double fprtol,
     free(rt);
     if (spmv_out) *spmv_out = ctx.spmv;
     return st.iters;
+}
+
+int orc_matexpre(const orc_problem *P, const cplx *r, cplx *w, double fprtol,
+                 int restart, int maxit, int fixed, int64_t *spmv_out)
+{
+    return orc_matexpre_v(P, 0, r, w, fprtol, restart, maxit, fixed, spmv_out);
 }
 
 /*
@@ -456,6 +489,7 @@ typedef struct {
     int calls;
     int *inner_log;
     int log_cap;
+    int variant;        /* preconditioner variant of orc_matexpre_v */
 } outer_ctx;
 
 static void helmholtz_op(void *vctx, const cplx *in, cplx *out)
@@ -469,8 +503,8 @@ static void matexpre_op(void *vctx, const cplx *in, cplx *out)
 {
     outer_ctx *c = vctx;
     int64_t sp = 0;
-    int it = orc_matexpre(c->P, in, out, c->fprtol, c->inner_restart, c->inner_maxit,
-                          c->inner_fixed, &sp);
+    int it = orc_matexpre_v(c->P, c->variant, in, out, c->fprtol, c->inner_restart,
+                            c->inner_maxit, c->inner_fixed, &sp);
     c->spmv += sp;
     if (c->inner_log && c->calls < c->log_cap) c->inner_log[c->calls] = it;
     c->calls++;
@@ -493,13 +527,14 @@ typedef struct {
  * every preconditioner application; res_log (nullable, capacity maxit) gets
  * the residual estimate after every outer iteration.
  */
-void orc_fgmres(const orc_problem *P, const cplx *b, cplx *u, double rtol, int restart,
-                int maxit, double fprtol, int inner_restart, int inner_maxit,
-                int inner_fixed, int *inner_log, int log_cap, double *res_log,
-                orc_solve_stats *out)
+void orc_fgmres_v(const orc_problem *P, int variant, const cplx *b, cplx *u, double rtol,
+                  int restart, int maxit, double fprtol, int inner_restart, int inner_maxit,
+                  int inner_fixed, int *inner_log, int log_cap, double *res_log,
+                  orc_solve_stats *out)
 {
     int64_t n = n_total(P);
-    outer_ctx ctx = {P, fprtol, inner_restart, inner_maxit, inner_fixed, 0, 0, inner_log, log_cap};
+    outer_ctx ctx = {P, fprtol, inner_restart, inner_maxit, inner_fixed, 0, 0, inner_log, log_cap,
+                     variant};
     double bn = vnorm(n, b);
     orc_krylov_stats st;
     fgmres_core(n, helmholtz_op, &ctx, matexpre_op, &ctx, b, u, rtol * bn, restart, maxit,
@@ -513,6 +548,15 @@ void orc_fgmres(const orc_problem *P, const cplx *b, cplx *u, double rtol, int r
     out->converged = st.converged && out->true_relres <= rtol;
     out->spmv = ctx.spmv + st.spmv + 1;
     free(r);
+}
+
+void orc_fgmres(const orc_problem *P, const cplx *b, cplx *u, double rtol, int restart,
+                int maxit, double fprtol, int inner_restart, int inner_maxit,
+                int inner_fixed, int *inner_log, int log_cap, double *res_log,
+                orc_solve_stats *out)
+{
+    orc_fgmres_v(P, 0, b, u, rtol, restart, maxit, fprtol, inner_restart, inner_maxit,
+                 inner_fixed, inner_log, log_cap, res_log, out);
 }
 
 /* Plain GMRES on A_s or A (no preconditioner), used by tests as a reference
