@@ -60,6 +60,9 @@ def parse_args():
     ap.add_argument("--profile-case", choices=["2d", "3d"], default=None,
                     help="run two exp actions of the 2D (1088^2) or 3D (288^3) workload "
                          "and exit; a small command for ncu captures")
+    ap.add_argument("--persist-cfg", type=int, default=None,
+                    help="with --profile-case 2d: force this persistent-kernel configuration "
+                         "(skips the autotuner's other candidates)")
     return ap.parse_args()
 
 
@@ -455,7 +458,8 @@ def run_profile_case(args):
     else:
         g, c, p, _ = workload()
     prob = N.Problem.from_grid(g, c, p)
-    prob.set_params(prec=args.prec, exp_tol=1e-12 if args.prec == "c128" else 1e-6)
+    kw = {} if args.persist_cfg is None else {"persist_cfg": args.persist_cfg}
+    prob.set_params(prec=args.prec, exp_tol=1e-12 if args.prec == "c128" else 1e-6, **kw)
     x = torch.ones(g.n_total, dtype=torch.complex128, device="cuda")
     y = prob.empty()
     for _ in range(2):

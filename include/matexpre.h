@@ -92,7 +92,10 @@ typedef struct {
  *  precond    preconditioner of mxp_apply_matexpre and mxp_solve: 0 = Algorithm 1
  *             (default); 1 = the truncated Neumann series of Sec. 3.2,
  *             P_N r = (sum_{n=0}^{N} exp(i t A_s)^n) psi_1(i t A_s) r (constant -i t
- *             dropped; a fixed linear map, no inner GMRES; Thm. 3.1)
+ *             dropped; a fixed linear map, no inner GMRES; Thm. 3.1); 2 = Algorithm 1's
+ *             steps on the second inverse formula of Sec. 3.1,
+ *             A^{-1} = -i t (I - psi_1(i t A))^{-1} psi_2(i t A): r~ = psi_2(i t A_s) r
+ *             and GMRES on (I - psi_1(i t A_s)) w = r~ to fprtol (w ~ (i/t) A_s^{-1} r)
  *  neumann_n  N of P_N (>= 0) */
 typedef struct {
     double omega, c_pml, shift_s, t, fprtol, exp_tol;
@@ -168,14 +171,18 @@ mxp_status mxp_get_params(const mxp_problem *prob, mxp_params *p);
 mxp_status mxp_apply_operator(mxp_problem *prob, int shifted, const void *x_dev,
                               void *y_dev);
 
-/* y = exp(i t A_s) x (which = 0) or y = psi_1(i t A_s) x (which = 1)
- * (Def. psi), in the problem's precision; x and y are complex128.
- * passes_out (nullable) receives the number of stencil sweeps. */
+/* y = exp(i t A_s) x (which = 0), psi_1(i t A_s) x (which = 1) or
+ * psi_2(i t A_s) x (which = 2) (Def. psi), in the problem's precision; x and y
+ * are complex128.  psi_1 and psi_2 are read off the exponential of the matrix
+ * augmented by one scalar row (psi_1) or a 2x2 Jordan block (psi_2).
+ * passes_out (nullable) receives the number of stencil sweeps.  MXP_EINVAL for
+ * any other which. */
 mxp_status mxp_apply_phi(mxp_problem *prob, int which, const void *x_dev, void *y_dev,
                          int64_t *passes_out);
 
-/* w = MatExPre(r): Algorithm 1 with the problem's parameters (or P_N r when
- * params.precond = 1; st->inner_iters then reports N).  st nullable.
+/* w = MatExPre(r): Algorithm 1 with the problem's parameters (P_N r when
+ * params.precond = 1, st->inner_iters then reporting N; the second inverse
+ * formula's variant when params.precond = 2).  st nullable.
  * Returns MXP_OK also when the inner GMRES stopped at inner_maxit (st->converged
  * tells which); MXP_ENAN if a residual became non-finite. */
 mxp_status mxp_apply_matexpre(mxp_problem *prob, const void *r_dev, void *w_dev,

@@ -101,8 +101,8 @@ struct mxp_problem {
     std::vector<double2> coef_host;   // [3][3][nmax]
     // shift and plans
     double mu = 0;
-    double nu = 0, nu_aug = 0;
-    TaylorPlan plan_exp, plan_psi;
+    double nu = 0, nu_aug = 0, nu_aug2 = 0;
+    TaylorPlan plan_exp, plan_psi, plan_psi2;
     int fused_cfg = -1;        // tile configuration of the fused 2D sweeps, -1 = unfused
     int fused_tyo = 0;         // output-tile height of the fused sweeps (0 = largest)
     double fused_cost = 1e30;  // estimated ms per exp action with the per-pass kernels
@@ -287,6 +287,7 @@ static void make_plans(mxp_problem *P)
 {
     P->plan_exp = make_plan(P->nu, P->prm.exp_tol, theta_of(P), exp_fuse(P));
     P->plan_psi = make_plan(P->nu_aug, P->prm.exp_tol * 0.1, theta_of(P), effective_fuse(P));
+    P->plan_psi2 = make_plan(P->nu_aug2, P->prm.exp_tol * 0.1, theta_of(P), effective_fuse(P));
 }
 
 // Per-step tau / h^2 of the exp plan for the persistent kernel.
@@ -333,6 +334,7 @@ static void update_plans(mxp_problem *P)
     P->mu = 0.5 * (a + b);
     P->nu = nu_of_mu(P, T, P->mu);
     P->nu_aug = std::max(P->nu, std::abs(P->prm.t * P->mu));
+    P->nu_aug2 = std::max(P->nu, std::abs(P->prm.t * P->mu) + 1.0);   // Jordan block of psi_2
     make_plans(P);
 }
 
@@ -385,7 +387,8 @@ static mxp_status validate_params(const mxp_params *p)
     if (p->tile_cfg < -1 || p->tile_cfg >= std::max(fused2d_num_cfgs(), fused3d_num_cfgs()))
         return fail(MXP_EINVAL, "tile_cfg out of range");
     if (p->persist_cfg < -2 || p->persist_cfg >= persist2d_num_cfgs()) return fail(MXP_EINVAL, "persist_cfg out of range");
-    if (p->precond != 0 && p->precond != 1) return fail(MXP_EINVAL, "precond must be 0 (Algorithm 1) or 1 (P_N)");
+    if (p->precond < 0 || p->precond > 2)
+        return fail(MXP_EINVAL, "precond must be 0 (Algorithm 1), 1 (P_N) or 2 (second inverse formula)");
     if (p->neumann_n < 0 || p->neumann_n > 10000) return fail(MXP_EINVAL, "neumann_n must lie in [0, 10000]");
     return MXP_OK;
 }
@@ -778,11 +781,40 @@ static mxp_status retune(mxp_problem *P)
 
 // which = 0: out = exp(i t A_s) x; which = 1: out = psi_1(i t A_s) x.
 // out_mode 1 returns x - result instead (the fixed-point operator of Eq. fixed-point).
+// Scalar part of the augmented matrix of a psi action (which = 1: psi_1, one
+// scalar; which = 2: psi_2, a 2x2 Jordan block; which = 0: none), advanced by
+// the same truncated Taylor-Horner recursion as the grid block.
+struct AugScalars {
+    int which;
+    cd rot, invS;
+    double S;
+    cd z1, z2;     // state at the sub-step start
+    cd g1, g2;     // Horner values within the sub-step
+    AugScalars(int w, cd r, int nsub) : which(w), rot(r), invS(1.0 / nsub), S(nsub)
+    {
+        z1 = (w == 1) ? cd(1.0) : cd(0.0);
+        z2 = (w == 2) ? cd(1.0) : cd(0.0);
+        g1 = z1;
+        g2 = z2;
+    }
+    void begin_substep() { g1 = z1; g2 = z2; }
+    // coefficient of v in the grid-block update of Horner step k
+    cd gamma(int k) const { return which ? g1 / (S * k) : cd(0.0); }
+    void step(int k)
+    {
+        const cd n1 = z1 + (rot * g1 + invS * g2) / (double)k;
+        const cd n2 = z2 + rot * g2 / (double)k;
+        g1 = n1;
+        g2 = n2;
+    }
+    void end_substep() { z1 = g1; z2 = g2; }
+};
+
 template <typename S>
 static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *out, int out_mode)
 {
     using C = typename St<S>::C;
-    const TaylorPlan &pl = which ? P->plan_psi : P->plan_exp;
+    const TaylorPlan &pl = which == 2 ? P->plan_psi2 : which ? P->plan_psi : P->plan_exp;
     S *b[3] = {(S *)P->hb[0], (S *)P->hb[1], (S *)P->hb[2]};
     S *vs = (S *)P->hb[3];
     const int64_t n = P->ntot;
@@ -797,7 +829,13 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
     const int Ssub = pl.S, m = pl.m;
     const cd rot(0.0, -t * P->mu / Ssub);                 // scalar row of the augmented matrix / S
     const cd final_rho = std::exp(cd(0.0, t * P->mu));    // e^{i t mu}
-    cd yxi = which ? cd(1.0) : cd(0.0);
+    // scalar rows of the augmented matrix (Def. psi): psi_1 adds one row whose
+    // state xi1 = 1 feeds v into the grid block; psi_2 adds a 2x2 Jordan block,
+    // xi1' = xi2, xi2 = 1.  After the shift by -i t mu each scalar also decays
+    // as e^{-i t mu tau}.  Per sub-step (time 1/S) the Horner recursion of the
+    // scalar part is g <- z + J g / k with J = [[rot, 1/S], [0, rot]], and the
+    // grid block takes g1 / (S k) times v.
+    AugScalars aug(which, rot, Ssub);
     StepScalars<C> sc;
     sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
     sc.mu = (sizeof(S) <= 8) ? (typename St<S>::R)0 : (typename St<S>::R)P->mu;  // float tables carry mu
@@ -842,16 +880,16 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
     if (cfg >= 0 && m % K == 0) {
         for (int sub = 0; sub < Ssub; ++sub) {
             int in = iy;
-            cd pxi = yxi;
+            aug.begin_substep();
             for (int k = m; k >= 1; k -= K) {
                 FusedStep steps[kMaxFuse];
                 for (int s = 0; s < K; ++s) {
                     const int kk = k - s;
-                    const cd gam = which ? pxi / ((double)Ssub * kk) : cd(0.0);
+                    const cd gam = aug.gamma(kk);
                     const bool last = (sub == Ssub - 1 && kk == 1);
                     steps[s] = FusedStep{t / ((double)Ssub * kk), gam.real(), gam.imag(),
                                          final_rho.real(), final_rho.imag(), last ? 1 : 0};
-                    pxi = yxi + rot * pxi / (double)kk;
+                    aug.step(kk);
                 }
                 const int o = (in == iy) ? (iy + 1) % 3 : 3 - iy - in;
                 fused_pass<S>(P, cfg, steps, b[in], b[iy], which ? vs : nullptr, b[o]);
@@ -859,7 +897,7 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
                 passes += K;
             }
             iy = in;
-            yxi = pxi;
+            aug.end_substep();
         }
         launch_convert_out<S>(b[iy], out, x, out_mode, n, st);
         P->passes += passes;
@@ -867,20 +905,20 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
     }
     for (int sub = 0; sub < Ssub; ++sub) {
         int in = iy;
-        cd pxi = yxi;
+        aug.begin_substep();
         for (int k = m; k >= 1; --k) {
             sc.sigma = PrecData<S>::c(cd(0.0, t / ((double)Ssub * k)));
-            sc.gamma = PrecData<S>::c(which ? pxi / ((double)Ssub * k) : cd(0.0));
+            sc.gamma = PrecData<S>::c(aug.gamma(k));
             sc.rho = PrecData<S>::c((sub == Ssub - 1 && k == 1) ? final_rho : cd(1.0));
             const int o = (in == iy) ? (iy + 1) % 3 : 3 - iy - in;
             launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc, b[in], b[iy],
                            which ? vs : nullptr, b[o], st);
-            pxi = yxi + rot * pxi / (double)k;
+            aug.step(k);
             in = o;
             ++passes;
         }
         iy = in;
-        yxi = pxi;
+        aug.end_substep();
     }
     launch_convert_out<S>(b[iy], out, x, out_mode, n, st);
     P->passes += passes;
@@ -937,7 +975,11 @@ static mxp_status matexpre_apply(mxp_problem *P, const double2 *r, double2 *w, m
     cudaStream_t st = P->stream;
     const int64_t passes0 = P->passes;
 
-    if (phi_dispatch(P, 1, r, P->rt, 0) < 0) return MXP_ECUDA;   // r~ = psi_1(i t A_s) r
+    // Algorithm 1: r~ = psi_1(i t A_s) r, operator I - exp(i t A_s); on the second
+    // inverse formula of Sec. 3.1 (precond = 2): r~ = psi_2 r, operator I - psi_1
+    const int rhs_which = P->prm.precond == 2 ? 2 : 1;
+    const int op_which = P->prm.precond == 2 ? 1 : 0;
+    if (phi_dispatch(P, rhs_which, r, P->rt, 0) < 0) return MXP_ECUDA;
     CK(cudaMemsetAsync(w, 0, n * sizeof(double2), st));
     krylov_nrm2sq(P->rt, n, a.hs.scal, P->ks, st);
     hess_start(a.hs, st);
@@ -957,7 +999,8 @@ static mxp_status matexpre_apply(mxp_problem *P, const double2 *r, double2 *w, m
         bool stop = false;
         for (; j < R && total < target; ++j) {
             // V[j+1] = (I - exp(i t A_s)) V[j]
-            if (phi_dispatch(P, 0, a.V + (size_t)j * n, a.V + (size_t)(j + 1) * n, 1) < 0) return MXP_ECUDA;
+            if (phi_dispatch(P, op_which, a.V + (size_t)j * n, a.V + (size_t)(j + 1) * n, 1) < 0)
+                return MXP_ECUDA;
             arnoldi_step(P, a, j);
             ++total;
             CK(cudaGetLastError());
@@ -971,7 +1014,7 @@ static mxp_status matexpre_apply(mxp_problem *P, const double2 *r, double2 *w, m
         krylov_maxpy(w, a.V, n, j, a.hs.y, 1.0, n, st);   // w += V y
         if (stop || total >= target) break;
         // restart: residual r~ - (I - exp) w
-        if (phi_dispatch(P, 0, w, P->tmp, 1) < 0) return MXP_ECUDA;
+        if (phi_dispatch(P, op_which, w, P->tmp, 1) < 0) return MXP_ECUDA;
         krylov_sub(P->tmp, P->rt, P->tmp, n, st);
         krylov_nrm2sq(P->tmp, n, a.hs.scal, P->ks, st);
         hess_start(a.hs, st);
@@ -1203,42 +1246,42 @@ static int batch_sweeps(mxp_problem *P, int which, int nb, const TaylorPlan &pl,
     const cd final_rho = std::exp(cd(0.0, t * P->mu));
     const int cfg = (sizeof(S) <= 8 && P->grid.dim == 2) ? P->fused_cfg : -1;
     const int K = cfg >= 0 ? fused2d_cfg_k(cfg) : 1;
-    cd yxi = which ? cd(1.0) : cd(0.0);
+    AugScalars aug(which, rot, Ssub);
     int iy = 0;
     StepScalars<C> sc;
     sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
     sc.mu = (sizeof(S) <= 8) ? (typename St<S>::R)0 : (typename St<S>::R)P->mu;
     for (int sub = 0; sub < Ssub; ++sub) {
         int in = iy;
-        cd pxi = yxi;
+        aug.begin_substep();
         for (int k = m; k >= 1; k -= K) {
             const int o = (in == iy) ? (iy + 1) % 3 : 3 - iy - in;
             if (cfg >= 0) {
                 FusedStep steps[kMaxFuse];
                 for (int s = 0; s < K; ++s) {
                     const int kk = k - s;
-                    const cd gam = which ? pxi / ((double)Ssub * kk) : cd(0.0);
+                    const cd gam = aug.gamma(kk);
                     steps[s] = FusedStep{t / ((double)Ssub * kk), gam.real(), gam.imag(), final_rho.real(),
                                          final_rho.imag(), (sub == Ssub - 1 && kk == 1) ? 1 : 0};
-                    pxi = yxi + rot * pxi / (double)kk;
+                    aug.step(kk);
                 }
                 launch_fused2d<S>(cfg, P->fused_tyo, P->geom, P->grid.npml, P->coef32, P->kappa32, steps,
                                   make_float2(1.0f, (float)P->prm.shift_s), 0.0f,
                                   (float)(1.0 / (P->grid.h * P->grid.h)), b[in], b[iy], vs, b[o], st, nb);
             } else {
                 sc.sigma = PrecData<S>::c(cd(0.0, t / ((double)Ssub * k)));
-                sc.gamma = PrecData<S>::c(which ? pxi / ((double)Ssub * k) : cd(0.0));
+                sc.gamma = PrecData<S>::c(aug.gamma(k));
                 sc.rho = PrecData<S>::c((sub == Ssub - 1 && k == 1) ? final_rho : cd(1.0));
                 for (int j = 0; j < nb; ++j)
                     launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc, b[in] + j * n,
                                    b[iy] + j * n, vs ? vs + j * n : nullptr, b[o] + j * n, st);
-                pxi = yxi + rot * pxi / (double)k;
+                aug.step(k);
             }
             in = o;
             *passes += K;
         }
         iy = in;
-        yxi = pxi;
+        aug.end_substep();
     }
     return iy;
 }
@@ -1730,7 +1773,7 @@ mxp_status mxp_apply_operator(mxp_problem *P, int shifted, const void *x_dev, vo
 mxp_status mxp_apply_phi(mxp_problem *P, int which, const void *x_dev, void *y_dev, int64_t *passes_out)
 {
     if (!P || !x_dev || !y_dev) return fail(MXP_EINVAL, "NULL argument");
-    if (which != 0 && which != 1) return fail(MXP_EINVAL, "which must be 0 (exp) or 1 (psi_1)");
+    if (which < 0 || which > 2) return fail(MXP_EINVAL, "which must be 0 (exp), 1 (psi_1) or 2 (psi_2)");
     DeviceGuard guard(P->device);
     CKS(ensure_base(P));
     const int64_t ps = phi_dispatch(P, which, (const double2 *)x_dev, (double2 *)y_dev, 0);
