@@ -98,6 +98,7 @@ struct mxp_problem {
     float *kappa32 = nullptr;
     double2 *coef64 = nullptr;
     float2 *coef32 = nullptr;
+    float2 *coef32s = nullptr;           // coef32 scaled by h^2 in double (persistent kernel)
     std::vector<double2> coef_host;   // [3][3][nmax]
     // shift and plans
     double mu = 0;
@@ -346,14 +347,17 @@ static mxp_status upload_coef32(mxp_problem *P)
 {
     const size_t cnt = P->coef_host.size();
     const int nm = P->geom.nmax;
-    std::vector<float2> c32(cnt);
+    const double h2 = P->grid.h * P->grid.h;
+    std::vector<float2> c32(cnt), c32s(cnt);
     for (size_t i = 0; i < cnt; ++i) {
         double re = P->coef_host[i].x;
         const size_t row = i / nm;
         if (row % 3 == 2 && (int)(row / 3) < P->grid.dim) re += P->mu / P->grid.dim;
         c32[i] = make_float2((float)re, (float)P->coef_host[i].y);
+        c32s[i] = make_float2((float)(re * h2), (float)(P->coef_host[i].y * h2));
     }
     CK(cudaMemcpyAsync(P->coef32, c32.data(), cnt * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->coef32s, c32s.data(), cnt * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
     CK(cudaStreamSynchronize(P->stream));
     return MXP_OK;
 }
@@ -435,8 +439,8 @@ static mxp_status ensure_base(mxp_problem *P)
     if (!P->host_scal) CK(cudaMallocHost(&P->host_scal, 8 * sizeof(double)));
     if (!P->bar) {
         // [0..3] grid-barrier words and error flag, [4..] per-tile pass epochs
-        CK(cudaMalloc(&P->bar, (4 + 4096) * sizeof(unsigned)));
-        CK(cudaMemsetAsync(P->bar, 0, (4 + 4096) * sizeof(unsigned), P->stream));
+        CK(cudaMalloc(&P->bar, kPersistBarWords * sizeof(unsigned)));
+        CK(cudaMemsetAsync(P->bar, 0, kPersistBarWords * sizeof(unsigned), P->stream));
     }
     return MXP_OK;
 }
@@ -598,7 +602,7 @@ static cudaError_t persist_action(mxp_problem *P, const S *x, S *out)
     const TaylorPlan &pl = P->plan_exp;
     const int K = persist2d_cfg_k(P->persist_cfg);
     const cd rho = std::exp(cd(0.0, P->prm.t * P->mu));
-    return launch_persist2d<S>(P->persist_cfg, P->geom, P->grid.npml, P->coef32, P->kappa32,
+    return launch_persist2d<S>(P->persist_cfg, P->geom, P->grid.npml, P->coef32s, P->kappa32,
                                make_float2(1.0f, (float)P->prm.shift_s),
                                (float)(P->grid.h * P->grid.h), P->tau_dev, pl.S * pl.m / K, pl.m / K,
                                make_float2((float)rho.real(), (float)rho.imag()), P->bar, P->p_txo,
@@ -1681,7 +1685,8 @@ mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, vo
         cudaMalloc(&P->kappa64, ntot * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&P->kappa32, ntot * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&P->coef64, cnt * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc(&P->coef32, cnt * sizeof(float2)) != cudaSuccess)
+        cudaMalloc(&P->coef32, cnt * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&P->coef32s, cnt * sizeof(float2)) != cudaSuccess)
         return bail(fail(MXP_ENOMEM, "device allocation failed"));
     if (cudaMemcpyAsync(P->c_dev, c_host, ntot * sizeof(double), cudaMemcpyHostToDevice, P->stream) != cudaSuccess)
         return bail(fail(MXP_ECUDA, "copy of the medium failed"));
@@ -1895,7 +1900,7 @@ void mxp_destroy(mxp_problem *P)
     DeviceGuard guard(P->device);
     cudaStreamSynchronize(P->stream);
     cudaFree(P->c_dev); cudaFree(P->kappa64); cudaFree(P->kappa32);
-    cudaFree(P->coef64); cudaFree(P->coef32);
+    cudaFree(P->coef64); cudaFree(P->coef32); cudaFree(P->coef32s);
     for (int i = 0; i < 4; ++i) cudaFree(P->hb[i]);
     cudaFree(P->rt); cudaFree(P->tmp); cudaFree(P->tmp2); cudaFree(P->bdev); cudaFree(P->xdev);
     cudaFree(P->ks.partials);

@@ -92,6 +92,13 @@ void launch_step(const Geom &g, const typename St<S>::C *coef, const typename St
 // result by rho.  cfg selects a tile shape (see fused2d.cu); returns false if
 // the configuration is not supported (then the caller uses launch_step).
 constexpr int kMaxFuse = 8;
+
+// Synchronisation words of the persistent exp kernel: [0] arrival count,
+// [1] generation, [2] error flag, [3] spare, then one epoch word per tile, each
+// in its own 32-byte sector (tiles poll their neighbours' words concurrently).
+constexpr int kPersistMaxTiles = 4096;
+constexpr int kPersistFlagStride = 8;
+constexpr size_t kPersistBarWords = 4 + (size_t)kPersistMaxTiles * kPersistFlagStride;
 struct FusedStep {
     double tau, gamma_re, gamma_im, rho_re, rho_im;
     int rho_on;

@@ -23,19 +23,18 @@ namespace mxp {
 struct PersistArgs {
     int n0, n1, nmax, npml;
     int txo, tyo, ntx, nty;      // tile extents and tile counts
-    const float2 *coef;
+    const float2 *coef;          // coefficient table scaled by h^2 (operator in dimensionless units)
     const float *kappa;
     float2 zfac;                 // 1 + i s
-    float h2;                    // h^2: operator scaled to dimensionless units
+    float h2;                    // h^2: scales kappa (1 + i s)
     const float *tau;            // per step: tau / h^2 (operator scaled by h^2), npass * K
     int npass, pass_per_sub;     // passes in total and per sub-step
-    float2 rho;                  // applied at the very last step
+    float2 rho;                  // e^{i t mu}: multiplies the result (undoes the shift)
     unsigned *bar;               // [0] arrival count, [1] generation, [2] error flag, [4..] tile epochs
 };
 
 constexpr long long kBarrierSpinLimit = 1ll << 24;   // x >= 32 ns sleep: about a second
 constexpr long long kNeighbourPollLimit = 1ll << 21;  // L2 polls (~0.5 us each): about a second
-constexpr int kMaxPersistTiles = 4096;               // tile epoch words after the barrier header
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks,
                                              long long limit = kBarrierSpinLimit)
@@ -73,25 +72,29 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks,
 // Point-to-point pass synchronisation: after publishing its strips for pass p a
 // CTA posts epoch p + 1, then waits until each of its (up to eight) neighbour
 // tiles has posted at least p + 1.  A CTA is therefore at most one pass ahead of
-// any neighbour, which keeps the two exchange buffers safe.  Bounded polling:
-// on timeout the error word is set and the caller stops.
+// any neighbour, which keeps the two exchange buffers safe.  Lanes 0..8 of warp
+// 0 poll one neighbour each (lane 4 is the tile itself), so the wait costs one
+// L2 round trip when the neighbours are already there.  Bounded polling: on
+// timeout the error word is set and the caller stops.
 __device__ __forceinline__ bool neighbour_sync(unsigned *bar, int bx, int by, int ntx, int nty,
                                                unsigned epoch)
 {
     __shared__ int s_ok2;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         volatile unsigned *flags = bar + 4;
         volatile unsigned *verr = bar + 2;
-        __threadfence();
-        atomicExch(bar + 4 + by * ntx + bx, epoch);
+        if (lane == 0) {
+            __threadfence();
+            atomicExch(bar + 4 + (by * ntx + bx) * kPersistFlagStride, epoch);
+        }
         int ok = 1;
-        for (int dy = -1; dy <= 1 && ok; ++dy)
-            for (int dx = -1; dx <= 1 && ok; ++dx) {
-                const int nx = bx + dx, ny = by + dy;
-                if ((dx == 0 && dy == 0) || nx < 0 || ny < 0 || nx >= ntx || ny >= nty) continue;
+        if (lane < 9 && lane != 4) {
+            const int nx = bx + lane % 3 - 1, ny = by + lane / 3 - 1;
+            if (nx >= 0 && ny >= 0 && nx < ntx && ny < nty) {
                 long long it = 0;
-                while (flags[ny * ntx + nx] < epoch) {
+                while (flags[(ny * ntx + nx) * kPersistFlagStride] < epoch) {
                     if (++it > kNeighbourPollLimit || *verr != 0u) {
                         atomicExch(bar + 2, 1u);
                         ok = 0;
@@ -99,8 +102,10 @@ __device__ __forceinline__ bool neighbour_sync(unsigned *bar, int bx, int by, in
                     }
                 }
             }
+        }
+        ok = __all_sync(0xffffffffu, ok);
         __threadfence();
-        s_ok2 = ok && (*verr == 0u);
+        if (lane == 0) s_ok2 = ok && (*verr == 0u);
     }
     __syncthreads();
     return s_ok2 != 0;
@@ -119,7 +124,7 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
     extern __shared__ float2 sm[];
     float2 *b0 = sm;
     float2 *b1 = sm + PY * PX;
-    float2 *cy = b1 + PY * PX;          // [BG*R][3] scaled y-axis coefficients wp, wm, wc of region rows
+    float2 *cy = b1 + PY * PX;          // [BG*R][3] y-axis coefficients wp, wm, wc of region rows
     float *ks = reinterpret_cast<float *>(cy + 3 * BG * R);   // [BG*R][BX] kappa of the region
 
     const int tx = threadIdx.x % BX;
@@ -142,9 +147,9 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
             wm = a.coef[4 * nm + gy];
             wc = a.coef[5 * nm + gy];
         }
-        cy[3 * r] = make_float2(wp.x * h2, wp.y * h2);
-        cy[3 * r + 1] = make_float2(wm.x * h2, wm.y * h2);
-        cy[3 * r + 2] = make_float2(wc.x * h2, wc.y * h2);
+        cy[3 * r] = wp;
+        cy[3 * r + 1] = wm;
+        cy[3 * r + 2] = wc;
     }
     float2 wpx = make_float2(0.f, 0.f), wmx = make_float2(0.f, 0.f), wcx = make_float2(0.f, 0.f);
     if (inx) {
@@ -152,9 +157,6 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
         wmx = a.coef[nm + gx];
         wcx = a.coef[2 * nm + gx];
     }
-    wpx = make_float2(wpx.x * h2, wpx.y * h2);
-    wmx = make_float2(wmx.x * h2, wmx.y * h2);
-    wcx = make_float2(wcx.x * h2, wcx.y * h2);
     const float2 zh = make_float2(a.zfac.x * h2, a.zfac.y * h2);
     __syncthreads();
 
@@ -191,7 +193,6 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
             const float2 *src = (s & 1) ? b1 : b0;
             float2 *dst = (s & 1) ? b0 : b1;
             const float tau = a.tau[pass * K + s];
-            const bool last = (pass == a.npass - 1) && (s == K - 1);
             const int r0 = grp * R;
             float2 up = src[r0 * PX + tx + 1];
             float2 cen = src[(r0 + 1) * PX + tx + 1];
@@ -240,7 +241,6 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
                     qy = fmaf(dx, cen.y, qy);
                     qy = fmaf(dy, cen.x, qy);
                     o[j] = make_float2(fmaf(-tau, qy, yr[c + j].x), fmaf(tau, qx, yr[c + j].y));
-                    if (last) o[j] = cmul(a.rho, o[j]);
                     up = cen;
                     cen = dn[j];
                 }
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
         for (int r = 0; r < R; ++r) {
             if ((tilemask >> r) & 1u) {
                 const int ry = grp * R + r;
-                St<S>::st(out, (int64_t)(gy0 + ry) * n0 + gx, b0[(ry + 1) * PX + tx + 1]);
+                St<S>::st(out, (int64_t)(gy0 + ry) * n0 + gx, cmul(a.rho, b0[(ry + 1) * PX + tx + 1]));
             }
         }
     }
@@ -347,7 +347,7 @@ bool plan_tiles(int n0, int n1, int slots, int K, int txmax, int tymax, int *txo
     if (n0 < 1 || n1 < 1 || slots < 1 || K < 1 || txmax < 1 || tymax < 1) return false;
     const int ntx_min = (n0 + txmax - 1) / txmax, nty_min = (n1 + tymax - 1) / tymax;
     if ((long)ntx_min * nty_min > slots) return false;
-    slots = std::min(slots, kMaxPersistTiles);   // per-tile epoch words available
+    slots = std::min(slots, kPersistMaxTiles);   // per-tile epoch words available
     long best_area = -1;
     for (int tx_n = ntx_min; tx_n <= n0 && tx_n <= slots; ++tx_n) {
         const int a = (n0 + tx_n - 1) / tx_n;
@@ -422,7 +422,7 @@ cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef
     a.bar = bar;
     void *args[] = {&a, (void *)&x, (void *)&ex0, (void *)&ex1, (void *)&out};
     const PCfg c = kPCfgs[id];
-    cudaError_t e = cudaMemsetAsync(bar, 0, (4 + (size_t)ntx * nty) * sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(bar, 0, (4 + (size_t)ntx * nty * kPersistFlagStride) * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     count_launch();
     return cudaLaunchCooperativeKernel(fn, dim3(ntx * nty), dim3(c.BX * c.BG), args, smem, st);
