@@ -307,7 +307,7 @@ struct PCfg {
     int K, BX, BG, R;
 };
 static const PCfg kPCfgs[] = {{2, 128, 4, 18}, {4, 96, 4, 28}, {4, 96, 8, 14}, {4, 96, 9, 12},
-                               {2, 128, 8, 10}};
+                               {2, 128, 8, 10}, {6, 96, 4, 28}};
 constexpr int kNumP = sizeof(kPCfgs) / sizeof(kPCfgs[0]);
 
 int persist2d_num_cfgs() { return kNumP; }
@@ -331,7 +331,8 @@ static void cfg_info(int id, void **fn, size_t *smem)
     case 1: *fn = kernel_ptr<S, 4, 96, 4, 28>(); *smem = smem_bytes<S, 4, 96, 4, 28>(); break;
     case 2: *fn = kernel_ptr<S, 4, 96, 8, 14>(); *smem = smem_bytes<S, 4, 96, 8, 14>(); break;
     case 3: *fn = kernel_ptr<S, 4, 96, 9, 12>(); *smem = smem_bytes<S, 4, 96, 9, 12>(); break;
-    default: *fn = kernel_ptr<S, 2, 128, 8, 10>(); *smem = smem_bytes<S, 2, 128, 8, 10>(); break;
+    case 4: *fn = kernel_ptr<S, 2, 128, 8, 10>(); *smem = smem_bytes<S, 2, 128, 8, 10>(); break;
+    default: *fn = kernel_ptr<S, 6, 96, 4, 28>(); *smem = smem_bytes<S, 6, 96, 4, 28>(); break;
     }
 }
 
