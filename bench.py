@@ -60,6 +60,10 @@ def parse_args():
     ap.add_argument("--profile-case", choices=["2d", "3d"], default=None,
                     help="run two exp actions of the 2D (1088^2) or 3D (288^3) workload "
                          "and exit; a small command for ncu captures")
+    ap.add_argument("--record-traffic", nargs=3, metavar=("KERNEL", "PREC", "NCU_CSV"), default=None,
+                    help="parse an ncu --csv --print-units base log of dram__bytes_read/write.sum "
+                         "for KERNEL (persist2d, fused2d or horner_step) and store the DRAM bytes per "
+                         "launch with the kernel source hash in profiles/traffic.json; then exit")
     ap.add_argument("--persist-cfg", type=int, default=None,
                     help="with --profile-case 2d: force this persistent-kernel configuration "
                          "(skips the autotuner's other candidates)")
@@ -227,6 +231,44 @@ def recorded_traffic(kernel, prec):
     except Exception:
         pass
     return None
+
+
+KERNEL_NAMES = {"horner_step": "k_step", "fused2d": "k_fused2d", "persist2d": "k_persist2d"}
+
+
+def record_traffic(kernel, prec, csv_path):
+    """DRAM bytes per launch of `kernel` from an ncu CSV log (one row per
+    launch and metric), stored with the hash of the kernel's source file."""
+    import csv
+    per_launch = {}
+    with open(csv_path, newline="") as fh:
+        rows = [r for r in csv.reader(fh) if r]
+    head = next(i for i, r in enumerate(rows) if "Metric Name" in r)
+    cols = rows[head]
+    iid, iname, imet, iunit, ival = (cols.index("ID"), cols.index("Kernel Name"),
+                                     cols.index("Metric Name"), cols.index("Metric Unit"),
+                                     cols.index("Metric Value"))
+    for r in rows[head + 1:]:
+        if len(r) <= ival or KERNEL_NAMES[kernel] not in r[iname]:
+            continue
+        if r[imet] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            if r[iunit] != "byte":
+                raise SystemExit(f"expected byte units (ncu --print-units base), got {r[iunit]}")
+            per_launch[r[iid]] = per_launch.get(r[iid], 0.0) + float(r[ival].replace(",", ""))
+    if not per_launch:
+        raise SystemExit(f"no {KERNEL_NAMES[kernel]} launches with DRAM metrics in {csv_path}")
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    rec = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            rec = json.load(fh)
+    rec[f"{kernel}:{prec}"] = {"dram_bytes_per_launch": sum(per_launch.values()) / len(per_launch),
+                               "launches": len(per_launch), "kernel_sha": kernel_hash(kernel),
+                               "source": os.path.basename(csv_path)}
+    with open(path, "w") as fh:
+        json.dump(rec, fh, indent=1, sort_keys=True)
+    print(json.dumps(rec[f"{kernel}:{prec}"]))
+    return 0
 
 
 def run_ours(args):
@@ -472,6 +514,8 @@ def run_profile_case(args):
 
 def main():
     args = parse_args()
+    if args.record_traffic:
+        return record_traffic(*args.record_traffic)
     if args.profile_case:
         return run_profile_case(args)
     if args.impl == "reference":
