@@ -13,6 +13,8 @@ Pinned functions (the pins live in ``tests/test_oracle_*.py``):
   matexpre   Algorithm 1               -- converged apply = (i/t) A_s^{-1} r
   fgmres     outer FGMRES              -- converged solution = direct solve
   neumann    P_N of Sec. 3.2           -- eigenvalues of P_N A (Thm. 3.1)
+  apply with sound-hard / absorbing faces  -- cosine-mode eigenpairs, plane-wave
+                                          consistency at second order, Im(lambda) >= 0
   phi(2), matexpre(variant=1)         -- psi_2 scalar closed form, dense expm of
              second inverse formula       the augmented matrix, converged apply =
                                           (i/t) A_s^{-1} r
@@ -52,7 +54,7 @@ class _Problem(ct.Structure):
     _fields_ = [("dim", ct.c_int), ("ni", ct.c_int * 3), ("npml", ct.c_int),
                 ("h", ct.c_double), ("omega", ct.c_double), ("cpml", ct.c_double),
                 ("shift", ct.c_double), ("t", ct.c_double),
-                ("c", ct.POINTER(ct.c_double))]
+                ("c", ct.POINTER(ct.c_double)), ("bc", ct.c_int * 6)]
 
 
 class _SolveStats(ct.Structure):
@@ -103,7 +105,9 @@ class Problem:
     """Discrete Helmholtz problem: grid (dim, interior cells, PML cells), medium
     c (numpy array of the full grid, x fastest), omega, C_pml, shift s and t."""
 
-    def __init__(self, dim, ni, npml, c, omega, shift, t, cpml=20.0, h=None):
+    BC = {"dirichlet": 0, "sound_hard": 1, "absorbing": 2}
+
+    def __init__(self, dim, ni, npml, c, omega, shift, t, cpml=20.0, h=None, bc=None):
         ni = tuple(int(v) for v in ni)
         self.dim = int(dim)
         self.ni = ni
@@ -125,11 +129,21 @@ class Problem:
         self._s.shift = self.shift
         self._s.t = self.t
         self._s.c = self.c.ctypes.data_as(ct.POINTER(ct.c_double))
+        self.set_bc(bc)
+
+    def set_bc(self, bc=None):
+        """Face conditions (x-, x+, y-, y+, z-, z+): names of BC or 0/1/2;
+        None = zero Dirichlet everywhere."""
+        bc = list(bc) if bc is not None else [0] * 6
+        bc = [self.BC[v] if isinstance(v, str) else int(v) for v in bc] + [0] * (6 - len(bc))
+        for f in range(6):
+            self._s.bc[f] = bc[f]
+        self.bc = tuple(bc[:6])
 
     @classmethod
-    def from_grid(cls, grid, c, params):
+    def from_grid(cls, grid, c, params, bc=None):
         return cls(grid.dim, grid.ni, grid.npml, c, params.omega, params.shift, params.t,
-                   params.cpml, grid.h)
+                   params.cpml, grid.h, bc)
 
     def _vec(self, x):
         x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128).reshape(-1))

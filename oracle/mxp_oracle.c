@@ -11,7 +11,9 @@
  *   orc_apply     finite-difference Helmholtz operator with PML and complex
  *                 shift (Eq. helmholtz; Eq. pml-1d-s, extended to 2D/3D by
  *                 stretching each axis; shifted operator A_s = A + i w^2 s D of
- *                 Sec. 3.4 "Numerical strategies").
+ *                 Sec. 3.4 "Numerical strategies"); faces zero Dirichlet by
+ *                 default, or sound-hard / first-order absorbing through ghost
+ *                 points (the mixed boundary conditions of Sec. 4, Marmousi-II).
  *   orc_phi       exp(M)v, psi_1(M)v and psi_2(M)v for M = i t A_s (Def. psi):
  *                 truncated Taylor series over sub-steps.
  *   orc_matexpre  Algorithm 1: r <- psi_1(i t A_s) r, then GMRES on
@@ -52,6 +54,8 @@ typedef struct {
     double shift;     /* complex shift s of A_s */
     double t;         /* time length t */
     const double *c;  /* wave speed at every unknown, x fastest */
+    int bc[6];        /* boundary condition of faces x-, x+, y-, y+, z-, z+:
+                         0 zero Dirichlet, 1 sound-hard, 2 first-order absorbing */
 } orc_problem;
 
 typedef struct {
@@ -111,11 +115,37 @@ static void stretch_arrays(const orc_problem *P, int d, cplx *a, cplx *bp, cplx 
 }
 
 /*
+ * Ghost value at a face (Sec. 4, Marmousi-II: a sound-hard surface and
+ * first-order absorbing boundaries [Engquist-Majda], discretised with ghost
+ * points).  The boundary lies midway between the last unknown u_0 and its ghost
+ * u_g; the face condition, written with the centred difference and the mean
+ * there, gives u_g = f u_0 with
+ *   zero Dirichlet           u = 0 beyond the grid      f = 0
+ *   sound-hard               du/dn = 0                   f = 1
+ *   first-order absorbing    du/dn = i k u, k = omega/c_p (outgoing waves for
+ *                            the e^{-i omega t} convention)
+ *                            (u_g - u_0)/h = i k (u_g + u_0)/2
+ *                                            f = (1 + i k h/2) / (1 - i k h/2)
+ */
+static cplx ghost_factor(const orc_problem *P, int face, double cp)
+{
+    switch (P->bc[face]) {
+    case 1: return 1.0;
+    case 2: {
+        double kh2 = 0.5 * P->omega / cp * P->h;
+        return (1.0 + I * kh2) / (1.0 - I * kh2);
+    }
+    default: return 0.0;
+    }
+}
+
+/*
  * y = A x (shifted = 0) or y = A_s x (shifted = 1).
  * (A x)_p = sum_d a_d(x_p) [ b_d(x_p + h/2)(x_{p+e_d} - x_p)
  *                           - b_d(x_p - h/2)(x_p - x_{p-e_d}) ] / h^2
  *           + omega^2 (1 + i s [shifted]) / c_p^2 x_p,
- * with a_d, b_d = 1/s_d and x = 0 outside the grid.
+ * with a_d, b_d = 1/s_d; a neighbour beyond the grid is the face's ghost value
+ * (zero for the default Dirichlet faces).
  */
 void orc_apply(const orc_problem *P, int shifted, const cplx *x, cplx *y)
 {
@@ -140,13 +170,13 @@ void orc_apply(const orc_problem *P, int shifted, const cplx *x, cplx *y)
                 int idx[3] = {i, j, k};
                 int64_t p = i + stride[1] * j + stride[2] * k;
                 cplx acc = 0.0;
+                double cp = P->c[p];
                 for (int d = 0; d < P->dim; ++d) {
                     int q = idx[d];
-                    cplx xp = (q + 1 < nn[d]) ? x[p + stride[d]] : 0.0;
-                    cplx xm = (q - 1 >= 0) ? x[p - stride[d]] : 0.0;
+                    cplx xp = (q + 1 < nn[d]) ? x[p + stride[d]] : ghost_factor(P, 2 * d + 1, cp) * x[p];
+                    cplx xm = (q - 1 >= 0) ? x[p - stride[d]] : ghost_factor(P, 2 * d, cp) * x[p];
                     acc += a[d][q] * (bp[d][q] * (xp - x[p]) - bm[d][q] * (x[p] - xm)) * ih2;
                 }
-                double cp = P->c[p];
                 acc += w2 * zfac / (cp * cp) * x[p];
                 y[p] = acc;
             }
@@ -202,7 +232,9 @@ double orc_norm_inf_tA(const orc_problem *P, int shifted)
                     cplx bm = inv_stretch(P, d, xq - 0.5 * P->h);
                     diag -= a * (bp + bm) * ih2;
                     if (idx[d] + 1 < nn[d]) off += cabs(a * bp) * ih2;
+                    else diag += a * bp * ghost_factor(P, 2 * d + 1, P->c[p]) * ih2;
                     if (idx[d] - 1 >= 0) off += cabs(a * bm) * ih2;
+                    else diag += a * bm * ghost_factor(P, 2 * d, P->c[p]) * ih2;
                 }
                 double row = P->t * (off + cabs(diag));
                 if (row > best) best = row;

@@ -177,6 +177,37 @@ def config_2d_homogeneous():
     return g, c, paper_params(g, c, ppw=10.0)
 
 
+# Face conditions (x-, x+, y-, y+) of the Marmousi-II case of Sec. 4: a
+# sound-hard water surface on top (the y- face; depth is the last axis) and
+# first-order absorbing conditions on the other faces.
+MARMOUSI_BC = ("absorbing", "absorbing", "sound_hard", "absorbing")
+BC_CODES = {"dirichlet": 0, "sound_hard": 1, "absorbing": 2}
+
+
+def marmousi_like(grid: Grid, seed: int, water_frac: float = 0.13, vwater: float = 1.5,
+                  vmin: float = 1.6, vmax: float = 4.7, grf_amp: float = 0.1,
+                  corr_cells: float = 20.0) -> np.ndarray:
+    """A seeded stand-in for the Marmousi-II velocity model (not available
+    here): a water layer of velocity ``vwater`` over the top ``water_frac`` of
+    the depth, above a layered sediment column (velocity increasing with depth
+    from vmin to vmax) times (1 + grf_amp g).  No PML is expected (npml = 0)."""
+    c = layered_grf(grid, seed, vmin=vmin, vmax=vmax, grf_amp=grf_amp, corr_cells=corr_cells)
+    rows = max(1, int(round(water_frac * grid.ni[-1])))
+    c[grid.npml:grid.npml + rows] = vwater
+    return c
+
+
+def config_2d_marmousi_like(nx: int = 1700, seed: int = SEED_BASE + 8000, ppw: float = 10.0):
+    """Marmousi-shaped 2D case: nx x round(nx * 1400 / 6800) cells (the
+    aspect ratio of the model in Sec. 4), no PML, ppw 10 w.r.t. the water
+    velocity, t = 40 h^2, s = 1/freq; use with MARMOUSI_BC and a source near the
+    surface, centred in x."""
+    ny = int(round(nx * 1400 / 6800))
+    g = Grid(2, (nx, ny), 0)
+    c = marmousi_like(g, seed)
+    return g, c, paper_params(g, c, ppw=ppw)
+
+
 def config_2d_layered(n_interior: int = 1024, npml: int = 32, seed: int = SEED_BASE + 1000):
     """1024^2 interior + 32-cell PML, layered 1.5-4.5 background with a +-15%
     Gaussian random field (correlation 20 cells), ppw 8 w.r.t. c_min."""
