@@ -163,6 +163,27 @@ mxp_status mxp_default_params(const mxp_grid *grid, double c_min, double ppw,
 mxp_status mxp_set_params(mxp_problem *prob, const mxp_params *p);
 mxp_status mxp_get_params(const mxp_problem *prob, mxp_params *p);
 
+/* Boundary condition of one face of the grid. */
+typedef enum {
+    MXP_BC_DIRICHLET = 0,   /* zero value beyond the grid (default; used with a PML) */
+    MXP_BC_SOUND_HARD = 1,  /* du/dn = 0 through a ghost point: u_ghost = u_p */
+    MXP_BC_ABSORBING = 2    /* first-order absorbing du/dn = i k u, k = omega / c_p:
+                               u_ghost = u_p (1 + i k h/2) / (1 - i k h/2) */
+} mxp_bc;
+
+/* Face conditions of the problem: bc[6] for the faces x-, x+, y-, y+, z-, z+
+ * (faces beyond the grid's dimension must be MXP_BC_DIRICHLET).  These are the
+ * mixed boundary conditions of the Marmousi-II case of Sec. 4 (a sound-hard
+ * surface and first-order absorbing sides and bottom, discretised with ghost
+ * points; normally with npml = 0).  The face lies midway between a boundary
+ * unknown and its ghost; the ghost's coefficient joins the diagonal of the
+ * boundary rows of A and A_s.  With any non-Dirichlet face the exp / psi
+ * actions use the per-pass unfused sweep (the tiled and persistent kernels
+ * assume zero ghosts).  Copies bc; allocates the face terms on the problem's
+ * device (MXP_ENOMEM on failure); MXP_EINVAL for an unknown code. */
+mxp_status mxp_set_boundary(mxp_problem *prob, const int *bc);
+mxp_status mxp_get_boundary(const mxp_problem *prob, int *bc);
+
 /* y = A x (shifted = 0) or y = A_s x (shifted = 1), complex128.
  * (A x)_p = sum_d a_d [b_d+ (x_{p+e_d} - x_p) - b_d- (x_p - x_{p-e_d})] / h^2
  *           + omega^2 (1 + i s [shifted]) / c_p^2 x_p, with a_d = 1/s_d at the

@@ -99,6 +99,13 @@ struct mxp_problem {
     double2 *coef64 = nullptr;
     float2 *coef32 = nullptr;
     float2 *coef32s = nullptr;           // coef32 scaled by h^2 in double (persistent kernel)
+    // ghost-point faces (mxp_set_boundary): condition per face, and the diagonal
+    // term of every boundary cell of a non-Dirichlet face (complex128 and complex64)
+    int bc[6] = {0, 0, 0, 0, 0, 0};
+    int nfaces = 0;
+    double2 *face64 = nullptr;
+    float2 *face32 = nullptr;
+    int64_t face_off[6] = {0, 0, 0, 0, 0, 0};
     std::vector<double2> coef_host;   // [3][3][nmax]
     // shift and plans
     double mu = 0;
@@ -466,13 +473,24 @@ template <typename S> struct PrecData;
 template <> struct PrecData<double2> {
     static const double2 *coef(const mxp_problem *P) { return P->coef64; }
     static const double *kappa(const mxp_problem *P) { return P->kappa64; }
+    static const double2 *faces(const mxp_problem *P) { return P->face64; }
     static double2 c(cd z) { return make_double2(z.real(), z.imag()); }
 };
 template <> struct PrecData<float2> {
     static const float2 *coef(const mxp_problem *P) { return P->coef32; }
     static const float *kappa(const mxp_problem *P) { return P->kappa32; }
+    static const float2 *faces(const mxp_problem *P) { return P->face32; }
     static float2 c(cd z) { return make_float2((float)z.real(), (float)z.imag()); }
 };
+
+// Point the sweep scalars at the ghost-point face terms of the problem.
+template <typename S>
+static void set_faces(const mxp_problem *P, StepScalars<typename St<S>::C> &sc)
+{
+    sc.nfaces = P->nfaces;
+    for (int f = 0; f < 6; ++f)
+        sc.face[f] = (P->bc[f] != MXP_BC_DIRICHLET) ? PrecData<S>::faces(P) + P->face_off[f] : nullptr;
+}
 template <> struct PrecData<__nv_bfloat162> : PrecData<float2> {};
 
 template <typename S>
@@ -766,6 +784,12 @@ static mxp_status retune(mxp_problem *P)
 {
     P->persist_cfg = -1;
     P->f3_cfg = -1;
+    if (P->nfaces) {
+        // the tiled and persistent sweeps assume zero ghosts: faces keep the unfused sweep
+        P->fused_cfg = -1;
+        make_plans(P);
+        return MXP_OK;
+    }
     if (P->grid.dim == 3) {
         if (P->prm.prec == MXP_C64) CKS(tune_fused3<float2>(P));
         else if (P->prm.prec == MXP_BF16S) CKS(tune_fused3<__nv_bfloat162>(P));
@@ -843,6 +867,7 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
     StepScalars<C> sc;
     sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
     sc.mu = (sizeof(S) <= 8) ? (typename St<S>::R)0 : (typename St<S>::R)P->mu;  // float tables carry mu
+    set_faces<S>(P, sc);
     int64_t passes = 0;
     int iy = 0;
     if (which == 0 && P->persist_cfg >= 0 && sizeof(S) <= 8) {
@@ -946,6 +971,7 @@ static void apply_op(mxp_problem *P, int shifted, const double2 *x, double2 *y)
     sc.sigma = make_double2(1.0, 0.0);
     sc.gamma = make_double2(0.0, 0.0);
     sc.rho = make_double2(1.0, 0.0);
+    set_faces<double2>(P, sc);
     launch_step<double2>(P->geom, P->coef64, P->kappa64, sc, x, nullptr, nullptr, y, P->stream);
     P->passes += 1;
 }
@@ -1255,6 +1281,7 @@ static int batch_sweeps(mxp_problem *P, int which, int nb, const TaylorPlan &pl,
     StepScalars<C> sc;
     sc.zfac = PrecData<S>::c(cd(1.0, P->prm.shift_s));
     sc.mu = (sizeof(S) <= 8) ? (typename St<S>::R)0 : (typename St<S>::R)P->mu;
+    set_faces<S>(P, sc);
     for (int sub = 0; sub < Ssub; ++sub) {
         int in = iy;
         aug.begin_substep();
@@ -1700,6 +1727,93 @@ mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, vo
     return MXP_OK;
 }
 
+// Diagonal terms of the ghost-point faces.  A face row's missing neighbour
+// coefficient w (a b-/h^2 at index 0, a b+/h^2 at index n_d - 1) multiplies the
+// ghost value f u_p: f = 1 on a sound-hard face; on a first-order absorbing face
+// (du/dn = i k u, k = omega / c_p, centred difference and mean at the face)
+// f = (1 + i k h/2) / (1 - i k h/2).
+static mxp_status build_faces(mxp_problem *P)
+{
+    const int dim = P->grid.dim, nm = P->geom.nmax;
+    const int n[3] = {P->geom.n[0], P->geom.n[1], P->geom.n[2]};
+    int64_t total = 0;
+    for (int f = 0; f < 2 * dim; ++f) {
+        P->face_off[f] = total;
+        if (P->bc[f] != MXP_BC_DIRICHLET) total += P->ntot / n[f / 2];
+    }
+    cudaFree(P->face64);
+    cudaFree(P->face32);
+    P->face64 = nullptr;
+    P->face32 = nullptr;
+    if (total == 0) return MXP_OK;
+    std::vector<double> c((size_t)P->ntot);
+    CK(cudaMemcpy(c.data(), P->c_dev, (size_t)P->ntot * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double2> f64((size_t)total);
+    std::vector<float2> f32((size_t)total);
+    const double h = P->grid.h, omega = P->prm.omega;
+    for (int f = 0; f < 2 * dim; ++f) {
+        if (P->bc[f] == MXP_BC_DIRICHLET) continue;
+        const int d = f / 2, side = f % 2;
+        const int e = side ? n[d] - 1 : 0;                       // index along the face normal
+        const double2 wv = P->coef_host[(size_t)(3 * d + (side ? 0 : 1)) * nm + e];
+        const cd w(wv.x, wv.y);
+        // the face's cells in the order the sweep indexes them: the two other
+        // axes, the lower one fastest
+        const int a0 = (d == 0) ? 1 : 0, a1 = (d == 2) ? 1 : 2;
+        const int m0 = n[a0], m1 = (dim == 3) ? n[a1] : 1;
+        for (int u1 = 0; u1 < m1; ++u1)
+            for (int u0 = 0; u0 < m0; ++u0) {
+                int idx[3] = {0, 0, 0};
+                idx[d] = e;
+                idx[a0] = u0;
+                if (dim == 3) idx[a1] = u1;
+                const int64_t q = idx[0] + (int64_t)n[0] * (idx[1] + (int64_t)n[1] * idx[2]);
+                cd gf(1.0);
+                if (P->bc[f] == MXP_BC_ABSORBING) {
+                    const double kh2 = 0.5 * omega / c[(size_t)q] * h;
+                    gf = cd(1.0, kh2) / cd(1.0, -kh2);
+                }
+                const cd term = w * gf;
+                const size_t o = (size_t)(P->face_off[f] + u0 + (int64_t)m0 * u1);
+                f64[o] = make_double2(term.real(), term.imag());
+                f32[o] = make_float2((float)term.real(), (float)term.imag());
+            }
+    }
+    CK(cudaMalloc(&P->face64, (size_t)total * sizeof(double2)));
+    CK(cudaMalloc(&P->face32, (size_t)total * sizeof(float2)));
+    CK(cudaMemcpyAsync(P->face64, f64.data(), (size_t)total * sizeof(double2), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->face32, f32.data(), (size_t)total * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    return MXP_OK;
+}
+
+mxp_status mxp_set_boundary(mxp_problem *P, const int *bc)
+{
+    if (!P || !bc) return fail(MXP_EINVAL, "NULL argument");
+    for (int f = 0; f < 6; ++f) {
+        if (bc[f] < MXP_BC_DIRICHLET || bc[f] > MXP_BC_ABSORBING) return fail(MXP_EINVAL, "unknown boundary condition");
+        if (f >= 2 * P->grid.dim && bc[f] != MXP_BC_DIRICHLET)
+            return fail(MXP_EINVAL, "faces beyond the grid's dimension must be MXP_BC_DIRICHLET");
+    }
+    DeviceGuard guard(P->device);
+    int nf = 0;
+    for (int f = 0; f < 6; ++f) {
+        P->bc[f] = bc[f];
+        nf += (bc[f] != MXP_BC_DIRICHLET);
+    }
+    P->nfaces = nf;
+    CKS(build_faces(P));
+    clear_graphs(P);
+    return retune(P);
+}
+
+mxp_status mxp_get_boundary(const mxp_problem *P, int *bc)
+{
+    if (!P || !bc) return fail(MXP_EINVAL, "NULL argument");
+    for (int f = 0; f < 6; ++f) bc[f] = P->bc[f];
+    return MXP_OK;
+}
+
 mxp_status mxp_set_params(mxp_problem *P, const mxp_params *p)
 {
     if (!P) return fail(MXP_EINVAL, "NULL problem");
@@ -1711,6 +1825,7 @@ mxp_status mxp_set_params(mxp_problem *P, const mxp_params *p)
     const bool recoef = np.omega != P->prm.omega || np.c_pml != P->prm.c_pml;
     P->prm = np;
     if (recoef) CKS(upload_coefs(P));
+    if (recoef && P->nfaces) CKS(build_faces(P));
     update_plans(P);
     CKS(upload_coef32(P));
     clear_graphs(P);
@@ -1901,6 +2016,7 @@ void mxp_destroy(mxp_problem *P)
     cudaStreamSynchronize(P->stream);
     cudaFree(P->c_dev); cudaFree(P->kappa64); cudaFree(P->kappa32);
     cudaFree(P->coef64); cudaFree(P->coef32); cudaFree(P->coef32s);
+    cudaFree(P->face64); cudaFree(P->face32);
     for (int i = 0; i < 4; ++i) cudaFree(P->hb[i]);
     cudaFree(P->rt); cudaFree(P->tmp); cudaFree(P->tmp2); cudaFree(P->bdev); cudaFree(P->xdev);
     cudaFree(P->ks.partials);

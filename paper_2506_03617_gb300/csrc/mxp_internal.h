@@ -76,6 +76,11 @@ template <typename C> struct StepScalars {
     C sigma;
     C gamma;
     C rho;
+    // ghost-point faces (x-, x+, y-, y+, z-, z+): diagonal term added on the
+    // boundary rows of a sound-hard or absorbing face, indexed by the cell's
+    // position on the face; nullptr = zero Dirichlet face.  nfaces = 0 skips all.
+    const C *face[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int nfaces = 0;
 };
 
 // ---------------------------------------------------------------- launchers

@@ -67,7 +67,22 @@ __global__ void __launch_bounds__(128) k_step(Geom g, const typename St<S>::C *_
     }
     const R kp = kappa[q];
     // diagonal: kappa (1 + i s) - mu - sum_d wc_d
-    const C diag = CT<C>::mk(kp * sc.zfac.x - sc.mu - wcs.x, kp * sc.zfac.y - wcs.y);
+    C diag = CT<C>::mk(kp * sc.zfac.x - sc.mu - wcs.x, kp * sc.zfac.y - wcs.y);
+    if (sc.nfaces) {
+        // rows on a sound-hard or absorbing face: the ghost value is a multiple of
+        // the row's own unknown, so its coefficient joins the diagonal
+        const int n0 = g.n[0], n1 = g.n[1];
+        if (sc.face[0] && i == 0) diag = cadd(diag, sc.face[0][j + (int64_t)n1 * k]);
+        if (sc.face[1] && i == n0 - 1) diag = cadd(diag, sc.face[1][j + (int64_t)n1 * k]);
+        if (DIM >= 2) {
+            if (sc.face[2] && j == 0) diag = cadd(diag, sc.face[2][i + (int64_t)n0 * k]);
+            if (sc.face[3] && j == n1 - 1) diag = cadd(diag, sc.face[3][i + (int64_t)n0 * k]);
+        }
+        if (DIM >= 3) {
+            if (sc.face[4] && k == 0) diag = cadd(diag, sc.face[4][i + (int64_t)n0 * j]);
+            if (sc.face[5] && k == g.n[2] - 1) diag = cadd(diag, sc.face[5][i + (int64_t)n0 * j]);
+        }
+    }
     acc = cadd(acc, cmul(diag, pc));
     C out = cmul(sc.sigma, acc);
     if (HAS_Y) out = cadd(out, St<S>::ld(y, q));

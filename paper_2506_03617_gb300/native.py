@@ -108,6 +108,8 @@ SIGNATURES = {
     "mxp_num_tile_configs": (ct.c_int, []),
     "mxp_tile_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_persist_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
+    "mxp_set_boundary": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
+    "mxp_get_boundary": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_persist_tile_plan": (ct.c_int, [ct.c_int] * 6 + [ct.POINTER(ct.c_int)] * 4),
     "mxp_destroy": (None, [ct.c_void_p]),
     "mxp_status_string": (ct.c_char_p, [ct.c_int]),
@@ -224,6 +226,21 @@ class Problem:
                 v = PRECISIONS[v]
             setattr(p, k, v)
         _check(self._lib.mxp_set_params(self._h, ct.byref(p)))
+
+    BC = {"dirichlet": 0, "sound_hard": 1, "absorbing": 2}
+
+    def set_boundary(self, bc=None):
+        """Face conditions (x-, x+, y-, y+, z-, z+) as names of BC or codes;
+        None = zero Dirichlet everywhere."""
+        codes = [self.BC[v] if isinstance(v, str) else int(v) for v in (bc or [])]
+        codes += [0] * (6 - len(codes))
+        arr = (ct.c_int * 6)(*codes[:6])
+        _check(self._lib.mxp_set_boundary(self._h, arr))
+
+    def boundary(self):
+        arr = (ct.c_int * 6)()
+        _check(self._lib.mxp_get_boundary(self._h, arr))
+        return tuple(arr)
 
     def tile_config(self):
         """(configuration index or -1 for the unfused sweep, fused step count)."""
