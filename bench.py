@@ -64,6 +64,11 @@ def parse_args():
                     help="parse an ncu --csv --print-units base log of dram__bytes_read/write.sum "
                          "for KERNEL (persist2d, fused2d or horner_step) and store the DRAM bytes per "
                          "launch with the kernel source hash in profiles/traffic.json; then exit")
+    ap.add_argument("--experiment", choices=["precond", "marmousi", "fused3d"], default=None,
+                    help="run one of the side measurements (one JSON line per case) and exit: "
+                         "precond = Algorithm 1 vs P_N vs the psi_2 variant on the 1088^2 "
+                         "workload; marmousi = mixed boundary conditions on a Marmousi-shaped "
+                         "grid vs a PML grid of the same size; fused3d = 3D sweep kernels")
     ap.add_argument("--persist-cfg", type=int, default=None,
                     help="with --profile-case 2d: force this persistent-kernel configuration "
                          "(skips the autotuner's other candidates)")
@@ -512,10 +517,96 @@ def run_profile_case(args):
     return 0
 
 
+def _timed_solve(prob, b, rtol=1e-6, maxit=300):
+    """One solve timed with CUDA events on the problem's stream; the true
+    relative residual is recomputed with the FP64 operator."""
+    import torch
+    x = prob.empty()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(prob.stream)
+    _, st = prob.solve(b, x, rtol=rtol, maxit=maxit, check=False)
+    ev1.record(prob.stream)
+    ev1.synchronize()
+    r = b - prob.apply_operator(x)
+    relres = float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b))
+    return {"seconds": ev0.elapsed_time(ev1) / 1e3, "outer": st["outer_iters"],
+            "inner_total": st["inner_iters_total"], "sweeps": st["stencil_passes"],
+            "converged": bool(st["converged"]), "true_relres": relres}
+
+
+def run_experiment(args):
+    import torch
+    from paper_2506_03617_gb300 import inputs as I
+    from paper_2506_03617_gb300 import native as N
+    prec = args.prec
+    tol = 1e-12 if prec == "c128" else 1e-6
+    if args.experiment == "precond":
+        grid, c, p, bh = workload()
+        b = torch.from_numpy(bh).cuda()
+        prob = N.Problem.from_grid(grid, c, p)
+        cases = [("alg1", dict(precond=0)), ("psi2_variant", dict(precond=2))]
+        cases += [(f"PN{n}", dict(precond=1, neumann_n=n)) for n in (4, 8, 16, 32)]
+        for name, kw in cases:
+            prob.set_params(prec=prec, exp_tol=tol, **kw)
+            _timed_solve(prob, b, maxit=20)                       # warm-up (tuning, first launches)
+            row = _timed_solve(prob, b, maxit=400)
+            print(json.dumps({"experiment": "precond", "workload": "2d_layered_1088", "prec": prec,
+                              "preconditioner": name, **row}), flush=True)
+    elif args.experiment == "marmousi":
+        g, c, p = I.config_2d_marmousi_like(nx=1700)
+        src = I.rhs_from_source(I.gaussian_source(g, center=(0.5, 2.5 * g.h))).ravel()
+        gp = I.Grid(2, g.ni, 32)                                  # same interior with a PML
+        cp = I.marmousi_like(gp, I.SEED_BASE + 8000)
+        pp = I.paper_params(gp, cp, ppw=10.0)
+        srcp = I.rhs_from_source(I.gaussian_source(gp, center=(0.5, 2.5 * gp.h))).ravel()
+        for name, grid, med, par, bh, bc in (("mixed_bc", g, c, p, src, I.MARMOUSI_BC),
+                                            ("pml", gp, cp, pp, srcp, None)):
+            prob = N.Problem.from_grid(grid, med, par)
+            prob.set_params(prec=prec, exp_tol=tol)
+            if bc:
+                prob.set_boundary(bc)
+            b = torch.from_numpy(bh).cuda()
+            _timed_solve(prob, b, maxit=2)
+            row = _timed_solve(prob, b, maxit=400)
+            print(json.dumps({"experiment": "marmousi", "case": name, "prec": prec,
+                              "grid": list(grid.n), "boundary": list(bc) if bc else "PML 32",
+                              "tuned": {"tile": prob.tile_config(), "persist": prob.persist_config()},
+                              "inner_per_outer": row["inner_total"] / max(row["outer"], 1),
+                              **row}), flush=True)
+            prob.close()
+    else:
+        g, c, p = I.config_3d_homogeneous()
+        prob = N.Problem.from_grid(g, c, p)
+        x = torch.ones(g.n_total, dtype=torch.complex128, device="cuda")
+        y = prob.empty()
+        cfgs = [("unfused", dict(fuse_k=1))] + [(f"fused3d_cfg{k}", dict(fuse_k=0, tile_cfg=k))
+                                                for k in range(4)]
+        for pr in ("c64", "bf16s"):
+            for name, kw in cfgs:
+                prob.set_params(prec=pr, exp_tol=1e-6, **kw)
+                prob.apply_phi(0, x, out=y)
+                torch.cuda.synchronize()
+                best, passes = 1e30, 0
+                for _ in range(2):
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record(prob.stream)
+                    passes = prob.apply_phi(0, x, out=y)[1]
+                    ev1.record(prob.stream)
+                    ev1.synchronize()
+                    best = min(best, ev0.elapsed_time(ev1) / 1e3)
+                print(json.dumps({"experiment": "fused3d", "workload": "3d_homogeneous_288", "prec": pr,
+                                  "kernel": name, "sweeps": passes, "ms": best * 1e3,
+                                  "gpts": g.n_total * passes / best / 1e9}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.record_traffic:
         return record_traffic(*args.record_traffic)
+    if args.experiment:
+        return run_experiment(args)
     if args.profile_case:
         return run_profile_case(args)
     if args.impl == "reference":

@@ -193,7 +193,7 @@ def marmousi_like(grid: Grid, seed: int, water_frac: float = 0.13, vwater: float
     from vmin to vmax) times (1 + grf_amp g).  No PML is expected (npml = 0)."""
     c = layered_grf(grid, seed, vmin=vmin, vmax=vmax, grf_amp=grf_amp, corr_cells=corr_cells)
     rows = max(1, int(round(water_frac * grid.ni[-1])))
-    c[grid.npml:grid.npml + rows] = vwater
+    c[:grid.npml + rows] = vwater           # with a PML, its top cells repeat the water value
     return c
 
 
