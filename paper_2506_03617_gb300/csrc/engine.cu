@@ -977,18 +977,24 @@ static void apply_op(mxp_problem *P, int shifted, const double2 *x, double2 *y)
 }
 
 // One Arnoldi step on V[0..j] -> V[j+1] (the new vector is already in V[j+1]):
-// classical Gram-Schmidt applied twice, normalisation and the Givens update.
+// classical Gram-Schmidt, repeated only when the first pass cancelled most of
+// w (decided on the device), normalisation and the Givens update.  The first
+// multi-dot also takes w itself (it is V[j+1]), which gives ||w||^2 for that
+// test without an extra pass.  On GB300 these complex128 passes are bound by
+// the FP64 pipe, so each skipped second pass halves their cost.
 static void arnoldi_step(mxp_problem *P, Arnoldi &a, int j)
 {
     const int64_t n = P->ntot;
     cudaStream_t st = P->stream;
     double2 *w = a.V + (size_t)(j + 1) * n;
     double2 *col = a.hs.H + (size_t)j * (a.R + 1);
-    krylov_mdot(a.V, n, j + 1, w, n, col, 0, P->ks, st);
+    double *gate = a.hs.scal + 6;
+    krylov_mdot(a.V, n, j + 2, w, n, col, 0, P->ks, st);          // col[j+1] = ||w||^2
+    krylov_reorth_gate(col, j, gate, st);
     krylov_maxpy(w, a.V, n, j + 1, col, -1.0, n, st);
-    krylov_mdot(a.V, n, j + 1, w, n, a.tmpcol, 0, P->ks, st);
-    krylov_maxpy(w, a.V, n, j + 1, a.tmpcol, -1.0, n, st);
-    krylov_addvec(col, a.tmpcol, j + 1, st);
+    krylov_mdot(a.V, n, j + 1, w, n, a.tmpcol, 0, P->ks, st, gate);
+    krylov_maxpy(w, a.V, n, j + 1, a.tmpcol, -1.0, n, st, gate);
+    krylov_addvec(col, a.tmpcol, j + 1, st, gate);
     krylov_nrm2sq(w, n, a.hs.scal, P->ks, st);
     krylov_scale_invnorm(w, w, a.hs.scal, n, st);
     hess_update(a.hs, j, st);

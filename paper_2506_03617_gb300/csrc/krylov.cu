@@ -20,13 +20,17 @@ __device__ __forceinline__ double2 warp_sum(double2 v)
 }
 
 // Block b writes partials[b * kChunk + i] = sum over its points of conj(V_i) w.
+// A launch with gate != nullptr does nothing unless *gate != 0 (device-side
+// decision of the selective second Gram-Schmidt pass).
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_mdot_partial(const double2 *__restrict__ V,
                                                               int64_t ld,
                                                               const double2 *__restrict__ w,
                                                               int64_t n,
-                                                              double2 *__restrict__ partials)
+                                                              double2 *__restrict__ partials,
+                                                              const double *__restrict__ gate)
 {
+    if (gate && *gate == 0.0) return;
     double2 acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = make_double2(0.0, 0.0);
@@ -57,8 +61,10 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot_partial(const double2 *__r
 
 // out[i] (+)= sum_b partials[b * kChunk + i], b in fixed order; one warp per i.
 __global__ void k_reduce_partials(const double2 *__restrict__ partials, int nblocks, int nv,
-                                  double2 *__restrict__ out, int accumulate)
+                                  double2 *__restrict__ out, int accumulate,
+                                  const double *__restrict__ gate)
 {
+    if (gate && *gate == 0.0) return;
     const int i = blockIdx.x;
     if (i >= nv) return;
     double2 s = make_double2(0.0, 0.0);
@@ -68,27 +74,30 @@ __global__ void k_reduce_partials(const double2 *__restrict__ partials, int nblo
 }
 
 void krylov_mdot(const double2 *V, int64_t ld, int nvec, const double2 *w, int64_t n,
-                 double2 *out, int accumulate, const KrylovScratch &ks, cudaStream_t st)
+                 double2 *out, int accumulate, const KrylovScratch &ks, cudaStream_t st,
+                 const double *gate)
 {
     for (int base = 0; base < nvec; base += kChunk) {
         const int nv = (nvec - base < kChunk) ? nvec - base : kChunk;
         const double2 *Vb = V + base * ld;
         switch (nv) {
 #define MXP_CASE(NVV) \
-    case NVV: count_launch(); k_mdot_partial<NVV><<<ks.grid, kRedThreads, 0, st>>>(Vb, ld, w, n, ks.partials); break;
+    case NVV: count_launch(); k_mdot_partial<NVV><<<ks.grid, kRedThreads, 0, st>>>(Vb, ld, w, n, ks.partials, gate); break;
             MXP_CASE(1) MXP_CASE(2) MXP_CASE(3) MXP_CASE(4)
             MXP_CASE(5) MXP_CASE(6) MXP_CASE(7) MXP_CASE(8)
 #undef MXP_CASE
         }
         count_launch();
-        k_reduce_partials<<<nv, 32, 0, st>>>(ks.partials, ks.grid, nv, out + base, accumulate);
+        k_reduce_partials<<<nv, 32, 0, st>>>(ks.partials, ks.grid, nv, out + base, accumulate, gate);
     }
 }
 
 // w += sign * sum_i coef[i] V_i
 __global__ void k_maxpy(double2 *__restrict__ w, const double2 *__restrict__ V, int64_t ld,
-                        int nvec, const double2 *__restrict__ coef, double sign, int64_t n)
+                        int nvec, const double2 *__restrict__ coef, double sign, int64_t n,
+                        const double *__restrict__ gate)
 {
+    if (gate && *gate == 0.0) return;
     __shared__ double2 cf[64];
     for (int i = threadIdx.x; i < nvec; i += blockDim.x)
         cf[i] = make_double2(sign * coef[i].x, sign * coef[i].y);
@@ -110,11 +119,11 @@ static int grid_for(int64_t n, int threads)
 }
 
 void krylov_maxpy(double2 *w, const double2 *V, int64_t ld, int nvec, const double2 *coef,
-                  double sign, int64_t n, cudaStream_t st)
+                  double sign, int64_t n, cudaStream_t st, const double *gate)
 {
     if (nvec <= 0) return;
     count_launch();
-    k_maxpy<<<grid_for(n, 256), 256, 0, st>>>(w, V, ld, nvec, coef, sign, n);
+    k_maxpy<<<grid_for(n, 256), 256, 0, st>>>(w, V, ld, nvec, coef, sign, n, gate);
 }
 
 __global__ void k_nrm_partial(const double2 *__restrict__ w, int64_t n, double2 *__restrict__ partials)
@@ -289,16 +298,37 @@ void hess_backsolve(const HessState &hs, int j, cudaStream_t st)
     k_hess_backsolve<<<1, 1, 0, st>>>(hs.H, hs.g, hs.y, j, hs.R);
 }
 
-__global__ void k_addvec(double2 *a, const double2 *b, int n)
+__global__ void k_addvec(double2 *a, const double2 *b, int n, const double *__restrict__ gate)
 {
+    if (gate && *gate == 0.0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = cadd(a[i], b[i]);
 }
 
-void krylov_addvec(double2 *a, const double2 *b, int n, cudaStream_t st)
+void krylov_addvec(double2 *a, const double2 *b, int n, cudaStream_t st, const double *gate)
 {
     count_launch();
-    k_addvec<<<(n + 63) / 64, 64, 0, st>>>(a, b, n);
+    k_addvec<<<(n + 63) / 64, 64, 0, st>>>(a, b, n, gate);
+}
+
+// Is a second classical Gram-Schmidt pass needed?  col[0..j] holds the first
+// pass's projections h_i and col[j+1].x the squared norm of w before them, so
+// ||w - V h||^2 = ||w||^2 - sum |h_i|^2 in exact arithmetic.  The pass is
+// repeated when the part of w left after the first pass is below eta ||w||
+// (the "twice is enough" test); the estimate only errs towards repeating.
+constexpr double kReorthEta2 = 0.01;   // eta^2, eta = 0.1
+__global__ void k_reorth_gate(const double2 *__restrict__ col, int j, double *__restrict__ gate)
+{
+    const double nw = col[j + 1].x;
+    double proj = 0.0;
+    for (int i = 0; i <= j; ++i) proj += col[i].x * col[i].x + col[i].y * col[i].y;
+    *gate = (nw - proj < kReorthEta2 * nw) ? 1.0 : 0.0;
+}
+
+void krylov_reorth_gate(const double2 *col, int j, double *gate, cudaStream_t st)
+{
+    count_launch();
+    k_reorth_gate<<<1, 1, 0, st>>>(col, j, gate);
 }
 
 __global__ void k_kappa(const double *__restrict__ c, double w2, double *__restrict__ k64,

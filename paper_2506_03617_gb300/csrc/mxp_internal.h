@@ -154,11 +154,16 @@ struct KrylovScratch {
 };
 constexpr int kChunk = 8;
 // out[i] (+)= sum_p conj(V_i[p]) w[p] for i < nvec; V_i = V + i * ld.
+// gate (nullable, device): when *gate == 0 the launches do nothing.
 void krylov_mdot(const double2 *V, int64_t ld, int nvec, const double2 *w, int64_t n,
-                 double2 *out, int accumulate, const KrylovScratch &ks, cudaStream_t st);
+                 double2 *out, int accumulate, const KrylovScratch &ks, cudaStream_t st,
+                 const double *gate = nullptr);
 // w += sign * sum_i coef[i] V_i  (coef on the device)
 void krylov_maxpy(double2 *w, const double2 *V, int64_t ld, int nvec, const double2 *coef,
-                  double sign, int64_t n, cudaStream_t st);
+                  double sign, int64_t n, cudaStream_t st, const double *gate = nullptr);
+// *gate = 1 if the first Gram-Schmidt pass left less than eta of ||w||
+// (col[0..j] = projections, col[j+1].x = ||w||^2 before them), else 0.
+void krylov_reorth_gate(const double2 *col, int j, double *gate, cudaStream_t st);
 // ||w||^2 into *out_dev (device double), deterministic
 void krylov_nrm2sq(const double2 *w, int64_t n, double *out_dev, const KrylovScratch &ks,
                    cudaStream_t st);
@@ -169,7 +174,7 @@ void krylov_scale_invnorm(double2 *w, const double2 *x, const double *nrm2sq_dev
 void krylov_sub(double2 *out, const double2 *a, const double2 *b, int64_t n, cudaStream_t st);
 void krylov_copy(double2 *out, const double2 *a, int64_t n, cudaStream_t st);
 void krylov_add(double2 *out, const double2 *a, int64_t n, cudaStream_t st);   // out += a
-void krylov_addvec(double2 *a, const double2 *b, int n, cudaStream_t st);
+void krylov_addvec(double2 *a, const double2 *b, int n, cudaStream_t st, const double *gate = nullptr);
 // kappa = omega^2 / c^2 in double and float
 void compute_kappa(const double *c, double omega, double *k64, float *k32, int64_t n,
                    cudaStream_t st);
