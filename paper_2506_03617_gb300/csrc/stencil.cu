@@ -91,6 +91,95 @@ __global__ void __launch_bounds__(128) k_step(Geom g, const typename St<S>::C *_
     St<S>::st(pout, q, out);
 }
 
+// The same Taylor-Horner step on a 3D grid, marching along z: a thread owns
+// one (x, y) column over a segment of LZ planes and keeps p at z-1, z and z+1 in
+// registers, so a point reads only the next plane of p from memory; its x and y
+// neighbours lie in the plane the neighbouring threads of the block load at the
+// same step (L1 hits).  DRAM traffic is then the compulsory p, y, kappa reads and
+// the p write of every point, plus two planes per segment.  Zero Dirichlet faces
+// only (faces with ghost terms use k_step).
+template <typename S, bool HAS_Y, bool HAS_V>
+__global__ void __launch_bounds__(256) k_step3z(Geom g, const typename St<S>::C *__restrict__ coef,
+                                                const typename St<S>::R *__restrict__ kappa,
+                                                StepScalars<typename St<S>::C> sc,
+                                                const S *__restrict__ pin, const S *__restrict__ y,
+                                                const S *__restrict__ v, S *__restrict__ pout, int lz)
+{
+    using C = typename St<S>::C;
+    using R = typename St<S>::R;
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2], nm = g.nmax;
+    if (i >= n0 || j >= n1) return;
+    const int z0 = blockIdx.z * lz;
+    const int z1 = min(z0 + lz, n2);
+    const int p0 = g.npml;
+    const bool xyin = g.fast && i >= p0 && i < n0 - p0 && j >= p0 && j < n1 - p0;
+    const C wpx = coef[i], wmx = coef[nm + i], wcx = coef[2 * nm + i];
+    const C wpy = coef[3 * nm + j], wmy = coef[4 * nm + j], wcy = coef[5 * nm + j];
+    const C *cz = coef + 6 * nm;
+    int64_t q = i + g.s1 * j + g.s2 * z0;
+    C pm = (z0 > 0) ? St<S>::ld(pin, q - g.s2) : czero<C>();
+    C pc = St<S>::ld(pin, q);
+    for (int k = z0; k < z1; ++k, q += g.s2) {
+        const C pp = (k + 1 < n2) ? St<S>::ld(pin, q + g.s2) : czero<C>();
+        const C xp = (i + 1 < n0) ? St<S>::ld(pin, q + 1) : czero<C>();
+        const C xm = (i > 0) ? St<S>::ld(pin, q - 1) : czero<C>();
+        const C yp = (j + 1 < n1) ? St<S>::ld(pin, q + g.s1) : czero<C>();
+        const C ym = (j > 0) ? St<S>::ld(pin, q - g.s1) : czero<C>();
+        const bool inner = xyin && k >= p0 && k < n2 - p0;
+        C acc;
+        if (inner) {
+            acc = cadd(cadd(cadd(xp, xm), cadd(yp, ym)), cadd(pp, pm));
+            const R s = (R)g.ih2;
+            acc = CT<C>::mk(acc.x * s, acc.y * s);
+        } else {
+            acc = cadd(cmul(wpx, xp), cmul(wmx, xm));
+            acc = cadd(acc, cadd(cmul(wpy, yp), cmul(wmy, ym)));
+            acc = cadd(acc, cadd(cmul(cz[k], pp), cmul(cz[nm + k], pm)));
+        }
+        const C wcs = cadd(cadd(wcx, wcy), cz[2 * nm + k]);
+        const R kp = kappa[q];
+        const C diag = CT<C>::mk(kp * sc.zfac.x - sc.mu - wcs.x, kp * sc.zfac.y - wcs.y);
+        acc = cadd(acc, cmul(diag, pc));
+        C out = cmul(sc.sigma, acc);
+        if (HAS_Y) out = cadd(out, St<S>::ld(y, q));
+        if (HAS_V) out = cadd(out, cmul(sc.gamma, St<S>::ld(v, q)));
+        out = cmul(sc.rho, out);
+        St<S>::st(pout, q, out);
+        pm = pc;
+        pc = pp;
+    }
+}
+
+// Planes per z segment: enough segments for about four waves of 256-thread
+// blocks at eight blocks per SM on 152 SMs, at least four planes each.
+static int z_segment(const Geom &g)
+{
+    const int64_t bxy = (int64_t)((g.n[0] + 31) / 32) * ((g.n[1] + 7) / 8);
+    const int64_t want = 152 * 8 * 4;
+    int64_t nseg = (want + bxy - 1) / bxy;
+    if (nseg < 1) nseg = 1;
+    int lz = (int)((g.n[2] + nseg - 1) / nseg);
+    if (lz < 4) lz = 4;
+    return lz;
+}
+
+template <typename S>
+static void launch_step3z(const Geom &g, const typename St<S>::C *coef, const typename St<S>::R *kappa,
+                          const StepScalars<typename St<S>::C> &sc, const S *pin, const S *y,
+                          const S *v, S *pout, cudaStream_t st)
+{
+    const int lz = z_segment(g);
+    dim3 block(32, 8);
+    dim3 grid((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + lz - 1) / lz);
+    count_launch();
+    if (y && v) k_step3z<S, true, true><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout, lz);
+    else if (y) k_step3z<S, true, false><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout, lz);
+    else if (v) k_step3z<S, false, true><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout, lz);
+    else k_step3z<S, false, false><<<grid, block, 0, st>>>(g, coef, kappa, sc, pin, y, v, pout, lz);
+}
+
 template <typename S, int DIM>
 static void launch_step_dim(const Geom &g, const typename St<S>::C *coef,
                             const typename St<S>::R *kappa,
@@ -111,6 +200,12 @@ void launch_step(const Geom &g, const typename St<S>::C *coef, const typename St
                  const StepScalars<typename St<S>::C> &sc, const S *pin, const S *y, const S *v,
                  S *pout, cudaStream_t st)
 {
+    if constexpr (sizeof(S) <= 8) {                                      // complex64 / bf16 storage
+        if (g.dim == 3 && sc.nfaces == 0) {
+            launch_step3z<S>(g, coef, kappa, sc, pin, y, v, pout, st);
+            return;
+        }
+    }
     if (g.dim == 3) launch_step_dim<S, 3>(g, coef, kappa, sc, pin, y, v, pout, st);
     else launch_step_dim<S, 2>(g, coef, kappa, sc, pin, y, v, pout, st);
 }
