@@ -244,6 +244,20 @@ int mxp_tile_config(const mxp_problem *prob, int *fuse_k);
 /* Persistent exp-action kernel in use (-1 = none) and its tile count. */
 int mxp_persist_config(const mxp_problem *prob, int *ntiles);
 
+/* Kernel that runs the exp-action sweeps of the problem (the choice of the
+ * autotuner and of the grid; no counterpart in the paper). */
+typedef enum {
+    MXP_SWEEP_POINTWISE = 0,      /* one launch per Taylor step, one thread per unknown */
+    MXP_SWEEP_FUSED_2D = 1,       /* K steps per launch on shared-memory tiles */
+    MXP_SWEEP_PERSISTENT_2D = 2,  /* one cooperative launch per action, grid held on chip */
+    MXP_SWEEP_FUSED_3D = 3,       /* K steps per launch by z-marching temporal blocking */
+    MXP_SWEEP_ZMARCH_3D = 4,      /* one launch per step, threads march along z in registers */
+    MXP_SWEEP_ZMARCH_TMA_3D = 5   /* one launch per step, planes staged by TMA (n0 % 4 == 0) */
+} mxp_sweep_kind;
+/* Returns an mxp_sweep_kind, or -1 for a NULL problem or a failed set-up.
+ * May build the problem's TMA descriptors (no other side effect). */
+int mxp_sweep_kernel(mxp_problem *prob);
+
 /* Tile planner of the persistent exp-action kernel (host only, no device
  * call; the paper has no counterpart).  Splits an n0 x n1 grid into at most
  * `slots` tiles of at most txmax x tymax cells, minimising the region (tile

@@ -106,6 +106,9 @@ struct mxp_problem {
     double2 *face64 = nullptr;
     float2 *face32 = nullptr;
     int64_t face_off[6] = {0, 0, 0, 0, 0, 0};
+    // tensor maps of the TMA-staged 3D sweep (built on first use per precision)
+    Tma3Maps *tma3 = nullptr;
+    int tma3_prec = -1;                  // precision the maps (or their absence) belong to
     std::vector<double2> coef_host;   // [3][3][nmax]
     // shift and plans
     double mu = 0;
@@ -809,6 +812,19 @@ static mxp_status retune(mxp_problem *P)
 
 // which = 0: out = exp(i t A_s) x; which = 1: out = psi_1(i t A_s) x.
 // out_mode 1 returns x - result instead (the fixed-point operator of Eq. fixed-point).
+// Tensor maps for the TMA-staged 3D sweep of this problem, or nullptr when the
+// grid or the driver does not allow them (the register-marching sweep is used).
+template <typename S>
+static const Tma3Maps *tma3_maps(mxp_problem *P)
+{
+    if (P->grid.dim != 3 || P->nfaces) return nullptr;
+    if (P->tma3_prec == (int)P->prm.prec) return P->tma3;
+    tma3_destroy(P->tma3);
+    P->tma3 = tma3_create<S>(P->geom, P->hb, P->kappa32);
+    P->tma3_prec = (int)P->prm.prec;
+    return P->tma3;
+}
+
 // Scalar part of the augmented matrix of a psi action (which = 1: psi_1, one
 // scalar; which = 2: psi_2, a 2x2 Jordan block; which = 0: none), advanced by
 // the same truncated Taylor-Horner recursion as the grid block.
@@ -940,8 +956,22 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
             sc.gamma = PrecData<S>::c(aug.gamma(k));
             sc.rho = PrecData<S>::c((sub == Ssub - 1 && k == 1) ? final_rho : cd(1.0));
             const int o = (in == iy) ? (iy + 1) % 3 : 3 - iy - in;
-            launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc, b[in], b[iy],
-                           which ? vs : nullptr, b[o], st);
+            bool done = false;
+            if constexpr (sizeof(S) <= 8) {
+                // 3D complex64 / bf16: planes staged by TMA (b[i] is work buffer i, v is buffer 3)
+                if (const Tma3Maps *tm = tma3_maps<S>(P)) {
+                    const cudaError_t ce = launch_step3z_tma<S>(P->geom, PrecData<S>::coef(P), sc, tm, in, iy,
+                                                                which ? 3 : -1, b[o], P->bar + 2, st);
+                    if (ce != cudaSuccess) {
+                        fail(MXP_ECUDA, std::string("TMA 3D sweep: ") + cudaGetErrorString(ce));
+                        return -1;
+                    }
+                    done = true;
+                }
+            }
+            if (!done)
+                launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc, b[in], b[iy],
+                               which ? vs : nullptr, b[o], st);
             aug.step(k);
             in = o;
             ++passes;
@@ -1813,6 +1843,20 @@ mxp_status mxp_set_boundary(mxp_problem *P, const int *bc)
     return retune(P);
 }
 
+int mxp_sweep_kernel(mxp_problem *P)
+{
+    if (!P) return -1;
+    if (P->persist_cfg >= 0) return MXP_SWEEP_PERSISTENT_2D;
+    if (P->grid.dim == 2) return P->fused_cfg >= 0 ? MXP_SWEEP_FUSED_2D : MXP_SWEEP_POINTWISE;
+    if (P->f3_cfg >= 0) return MXP_SWEEP_FUSED_3D;
+    if (P->prm.prec == MXP_C128) return MXP_SWEEP_POINTWISE;
+    if (P->nfaces) return MXP_SWEEP_POINTWISE;
+    DeviceGuard guard(P->device);
+    if (ensure_base(P) != MXP_OK) return -1;
+    const Tma3Maps *tm = (P->prm.prec == MXP_C64) ? tma3_maps<float2>(P) : tma3_maps<__nv_bfloat162>(P);
+    return tm ? MXP_SWEEP_ZMARCH_TMA_3D : MXP_SWEEP_ZMARCH_3D;
+}
+
 mxp_status mxp_get_boundary(const mxp_problem *P, int *bc)
 {
     if (!P || !bc) return fail(MXP_EINVAL, "NULL argument");
@@ -2024,6 +2068,7 @@ void mxp_destroy(mxp_problem *P)
     cudaFree(P->coef64); cudaFree(P->coef32); cudaFree(P->coef32s);
     cudaFree(P->face64); cudaFree(P->face32);
     for (int i = 0; i < 4; ++i) cudaFree(P->hb[i]);
+    tma3_destroy(P->tma3);
     cudaFree(P->rt); cudaFree(P->tmp); cudaFree(P->tmp2); cudaFree(P->bdev); cudaFree(P->xdev);
     cudaFree(P->ks.partials);
     cudaFree(P->tau_dev);

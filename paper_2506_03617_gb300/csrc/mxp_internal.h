@@ -83,6 +83,22 @@ template <typename C> struct StepScalars {
     int nfaces = 0;
 };
 
+// TMA-staged 3D sweep (tma3d.cu): tensor maps of the four 16-byte-per-unknown
+// work buffers (as p with halo and as y / v tiles) and of kappa; nullptr when
+// the grid does not qualify (3D with n0 a multiple of 4, 16-byte aligned
+// buffers) or the driver offers no tensor-map encoder.
+struct Tma3Maps;
+template <typename S>
+Tma3Maps *tma3_create(const Geom &g, void *const *bufs, const float *kappa);
+void tma3_destroy(Tma3Maps *t);
+// pout = one Taylor-Horner step as launch_step, reading p from buffer ip, y
+// from buffer iy and v from buffer iv (-1 = none); err receives 1 on a wait
+// timeout.
+template <typename S>
+cudaError_t launch_step3z_tma(const Geom &g, const typename St<S>::C *coef,
+                              const StepScalars<typename St<S>::C> &sc, const Tma3Maps *t, int ip,
+                              int iy, int iv, S *pout, unsigned *err, cudaStream_t st);
+
 // ---------------------------------------------------------------- launchers
 // coef: [dim][3][nmax] complex table: row 0 = a b+ / h^2, row 1 = a b- / h^2,
 // row 2 = their sum (a = 1/s at the node, b+- = 1/s at the half nodes).

@@ -110,6 +110,7 @@ SIGNATURES = {
     "mxp_persist_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_set_boundary": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_get_boundary": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
+    "mxp_sweep_kernel": (ct.c_int, [ct.c_void_p]),
     "mxp_persist_tile_plan": (ct.c_int, [ct.c_int] * 6 + [ct.POINTER(ct.c_int)] * 4),
     "mxp_destroy": (None, [ct.c_void_p]),
     "mxp_status_string": (ct.c_char_p, [ct.c_int]),
@@ -247,6 +248,15 @@ class Problem:
         k = ct.c_int(0)
         cfg = self._lib.mxp_tile_config(self._h, ct.byref(k))
         return int(cfg), int(k.value)
+
+    SWEEP_KINDS = ("pointwise", "fused_2d", "persistent_2d", "fused_3d", "zmarch_3d", "zmarch_tma_3d")
+
+    def sweep_kernel(self):
+        """Name of the kernel that runs this problem's exp-action sweeps."""
+        k = self._lib.mxp_sweep_kernel(self._h)
+        if k < 0:
+            _check(1)
+        return self.SWEEP_KINDS[k]
 
     def persist_config(self):
         """(persistent exp kernel configuration or -1, number of tiles)."""
