@@ -148,9 +148,10 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
         return reinterpret_cast<S *>(stg + st * SB + G::al(G::PBYTES) + (HAS_Y ? G::al(G::YBYTES) : 0) +
                                      G::al(G::KBYTES));
     };
-    // plane index pi (0 .. nplanes-1) is plane z0 - 1 + pi, held by stage pi % kStages
-    auto issue = [&](int pi) {
-        const int st = pi % kStages, z = z0 - 1 + pi;
+    // plane index pi (0 .. nplanes-1) is plane z0 - 1 + pi, held by stage pi % kStages;
+    // stage numbers and mbarrier parities advance incrementally
+    auto issue = [&](int pi, int st) {
+        const int z = z0 - 1 + pi;
         mbar_expect(&bar[st], TXB);
         tma_load3(p_of(st), &mp, E * (x0 - HL), y0 - 1, z, &bar[st]);
         if (HAS_Y) tma_load3(y_of(st), &my, E * x0, y0, z, &bar[st]);
@@ -165,9 +166,14 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
         s_fail = 0;
     }
     __syncthreads();
-    int issued = 0;                           // meaningful in thread 0 only
+    // producer / waiter state, used by thread 0 only
+    int issued = 0, is_stage = 0;             // next plane to load and its stage
+    int waited = -1, w_stage = 0, w_par = 0;  // planes 0 .. waited resident; next stage to wait on
     if (tid == 0) {
-        for (; issued < kStages && issued < nplanes; ++issued) issue(issued);
+        for (; issued < kStages && issued < nplanes; ++issued) {
+            issue(issued, is_stage);
+            if (++is_stage == kStages) is_stage = 0;
+        }
     }
 
     // per-column coefficients (constant along z)
@@ -181,24 +187,30 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
     const bool xyin = g.fast && i >= p0 && i < n0 - p0 && j >= p0 && j < n1 - p0;
     const int cidx = (ty + 1) * PW + tx + HL;
     const int tidx = ty * kTX + tx;
-    int waited = -1;                          // planes 0 .. waited are resident
+    int sm_ = 0, sc_ = 1, sp_ = 2;            // stages of planes pi - 1, pi, pi + 1
+    S *outp = pout + (i + g.s1 * j + g.s2 * z0);
 
-    for (int k = z0; k < z1; ++k) {
+    for (int k = z0; k < z1; ++k, outp += g.s2) {
         const int pi = k - z0 + 1;            // plane index of z = k
-        // planes pi - 1, pi, pi + 1 must be resident
-        bool ok = true;
-        while (waited < pi + 1 && ok) {
-            ++waited;
-            ok = mbar_wait(&bar[waited % kStages], (unsigned)((waited / kStages) & 1));
-        }
-        if (!ok) {
-            if (tid == 0) atomicExch(err, 1u);
-            s_fail = 1;
+        // thread 0 waits until planes pi - 1, pi, pi + 1 are resident; the block
+        // barrier then orders those TMA writes before every thread's reads
+        if (tid == 0) {
+            bool ok = true;
+            while (waited < pi + 1) {
+                ok = mbar_wait(&bar[w_stage], (unsigned)w_par);
+                if (!ok) break;
+                ++waited;
+                if (++w_stage == kStages) { w_stage = 0; w_par ^= 1; }
+            }
+            if (!ok) {
+                atomicExch(err, 1u);
+                s_fail = 1;
+            }
         }
         __syncthreads();
         if (s_fail) break;
         if (active) {
-            const S *pc_ = p_of(pi % kStages), *pm_ = p_of((pi - 1) % kStages), *pp_ = p_of((pi + 1) % kStages);
+            const S *pc_ = p_of(sc_), *pm_ = p_of(sm_), *pp_ = p_of(sp_);
             const C pc = sm_ld<S>(pc_, cidx);
             const C xp = sm_ld<S>(pc_, cidx + 1), xm = sm_ld<S>(pc_, cidx - 1);
             const C yp = sm_ld<S>(pc_, cidx + PW), ym = sm_ld<S>(pc_, cidx - PW);
@@ -215,22 +227,30 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
                 acc = cadd(acc, cadd(cmul(cz[k], pp), cmul(cz[nm + k], pm)));
             }
             const C wcs = cadd(cadd(wcx, wcy), cz[2 * nm + k]);
-            const R kp = k_of(pi % kStages)[tidx];
+            const R kp = k_of(sc_)[tidx];
             const C diag = CT<C>::mk(kp * sc.zfac.x - sc.mu - wcs.x, kp * sc.zfac.y - wcs.y);
             acc = cadd(acc, cmul(diag, pc));
             C out = cmul(sc.sigma, acc);
-            if (HAS_Y) out = cadd(out, sm_ld<S>(y_of(pi % kStages), tidx));
-            if (HAS_V) out = cadd(out, cmul(sc.gamma, sm_ld<S>(v_of(pi % kStages), tidx)));
+            if (HAS_Y) out = cadd(out, sm_ld<S>(y_of(sc_), tidx));
+            if (HAS_V) out = cadd(out, cmul(sc.gamma, sm_ld<S>(v_of(sc_), tidx)));
             out = cmul(sc.rho, out);
-            St<S>::st(pout, i + g.s1 * j + g.s2 * k, out);
+            St<S>::st(outp, 0, out);
         }
         __syncthreads();                      // stage of plane pi - 1 is free
-        if (tid == 0 && issued < nplanes) issue(issued++);
+        if (tid == 0 && issued < nplanes) {
+            issue(issued++, is_stage);        // is_stage == sm_ here
+            if (++is_stage == kStages) is_stage = 0;
+        }
+        sm_ = sc_;
+        sc_ = sp_;
+        if (++sp_ == kStages) sp_ = 0;
     }
     // loads issued but never waited for (only after a timeout): wait, bounded
     if (tid == 0) {
-        for (int pi = waited + 1; pi < issued; ++pi)
-            if (!mbar_wait(&bar[pi % kStages], (unsigned)((pi / kStages) & 1))) break;
+        for (; waited + 1 < issued; ++waited) {
+            if (!mbar_wait(&bar[w_stage], (unsigned)w_par)) break;
+            if (++w_stage == kStages) { w_stage = 0; w_par ^= 1; }
+        }
     }
 }
 
