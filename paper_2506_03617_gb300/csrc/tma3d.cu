@@ -139,24 +139,20 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
     const bool active = i < n0 && j < n1;
     const int nplanes = z1 - z0 + 2;          // planes z0-1 .. z1
 
-    auto p_of = [&](int st) { return reinterpret_cast<S *>(stg + st * SB); };
-    auto y_of = [&](int st) { return reinterpret_cast<S *>(stg + st * SB + G::al(G::PBYTES)); };
-    auto k_of = [&](int st) {
-        return reinterpret_cast<float *>(stg + st * SB + G::al(G::PBYTES) + (HAS_Y ? G::al(G::YBYTES) : 0));
-    };
-    auto v_of = [&](int st) {
-        return reinterpret_cast<S *>(stg + st * SB + G::al(G::PBYTES) + (HAS_Y ? G::al(G::YBYTES) : 0) +
-                                     G::al(G::KBYTES));
-    };
+    // byte offsets of the parts of a stage
+    constexpr int OY = G::al(G::PBYTES);
+    constexpr int OK = OY + (HAS_Y ? G::al(G::YBYTES) : 0);
+    constexpr int OV = OK + G::al(G::KBYTES);
     // plane index pi (0 .. nplanes-1) is plane z0 - 1 + pi, held by stage pi % kStages;
     // stage numbers and mbarrier parities advance incrementally
     auto issue = [&](int pi, int st) {
         const int z = z0 - 1 + pi;
+        unsigned char *b = stg + st * SB;
         mbar_expect(&bar[st], TXB);
-        tma_load3(p_of(st), &mp, E * (x0 - HL), y0 - 1, z, &bar[st]);
-        if (HAS_Y) tma_load3(y_of(st), &my, E * x0, y0, z, &bar[st]);
-        tma_load3(k_of(st), &mk, x0, y0, z, &bar[st]);
-        if (HAS_V) tma_load3(v_of(st), &mv, E * x0, y0, z, &bar[st]);
+        tma_load3(b, &mp, E * (x0 - HL), y0 - 1, z, &bar[st]);
+        if (HAS_Y) tma_load3(b + OY, &my, E * x0, y0, z, &bar[st]);
+        tma_load3(b + OK, &mk, x0, y0, z, &bar[st]);
+        if (HAS_V) tma_load3(b + OV, &mv, E * x0, y0, z, &bar[st]);
     };
 
     if (tid == 0) {
@@ -189,6 +185,8 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
     const int tidx = ty * kTX + tx;
     int sm_ = 0, sc_ = 1, sp_ = 2;            // stages of planes pi - 1, pi, pi + 1
     S *outp = pout + (i + g.s1 * j + g.s2 * z0);
+    // z-axis coefficients of the current plane, loaded one plane ahead
+    C czp = cz[z0], czm = cz[nm + z0], czc = cz[2 * nm + z0];
 
     for (int k = z0; k < z1; ++k, outp += g.s2) {
         const int pi = k - z0 + 1;            // plane index of z = k
@@ -209,8 +207,13 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
         }
         __syncthreads();
         if (s_fail) break;
+        const int kn = (k + 1 < n2) ? k + 1 : k;
+        const C czp_n = cz[kn], czm_n = cz[nm + kn], czc_n = cz[2 * nm + kn];
         if (active) {
-            const S *pc_ = p_of(sc_), *pm_ = p_of(sm_), *pp_ = p_of(sp_);
+            const unsigned char *bc = stg + sc_ * SB;
+            const S *pc_ = reinterpret_cast<const S *>(bc);
+            const S *pm_ = reinterpret_cast<const S *>(stg + sm_ * SB);
+            const S *pp_ = reinterpret_cast<const S *>(stg + sp_ * SB);
             const C pc = sm_ld<S>(pc_, cidx);
             const C xp = sm_ld<S>(pc_, cidx + 1), xm = sm_ld<S>(pc_, cidx - 1);
             const C yp = sm_ld<S>(pc_, cidx + PW), ym = sm_ld<S>(pc_, cidx - PW);
@@ -224,15 +227,15 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
             } else {
                 acc = cadd(cmul(wpx, xp), cmul(wmx, xm));
                 acc = cadd(acc, cadd(cmul(wpy, yp), cmul(wmy, ym)));
-                acc = cadd(acc, cadd(cmul(cz[k], pp), cmul(cz[nm + k], pm)));
+                acc = cadd(acc, cadd(cmul(czp, pp), cmul(czm, pm)));
             }
-            const C wcs = cadd(cadd(wcx, wcy), cz[2 * nm + k]);
-            const R kp = k_of(sc_)[tidx];
+            const C wcs = cadd(cadd(wcx, wcy), czc);
+            const R kp = reinterpret_cast<const float *>(bc + OK)[tidx];
             const C diag = CT<C>::mk(kp * sc.zfac.x - sc.mu - wcs.x, kp * sc.zfac.y - wcs.y);
             acc = cadd(acc, cmul(diag, pc));
             C out = cmul(sc.sigma, acc);
-            if (HAS_Y) out = cadd(out, sm_ld<S>(y_of(sc_), tidx));
-            if (HAS_V) out = cadd(out, cmul(sc.gamma, sm_ld<S>(v_of(sc_), tidx)));
+            if (HAS_Y) out = cadd(out, sm_ld<S>(reinterpret_cast<const S *>(bc + OY), tidx));
+            if (HAS_V) out = cadd(out, cmul(sc.gamma, sm_ld<S>(reinterpret_cast<const S *>(bc + OV), tidx)));
             out = cmul(sc.rho, out);
             St<S>::st(outp, 0, out);
         }
@@ -244,6 +247,9 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
         sm_ = sc_;
         sc_ = sp_;
         if (++sp_ == kStages) sp_ = 0;
+        czp = czp_n;
+        czm = czm_n;
+        czc = czc_n;
     }
     // loads issued but never waited for (only after a timeout): wait, bounded
     if (tid == 0) {
