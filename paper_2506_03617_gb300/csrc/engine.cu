@@ -122,6 +122,12 @@ struct mxp_problem {
     int p_txo = 0, p_tyo = 0, p_ntx = 0, p_nty = 0;
     float *tau_dev = nullptr;  // per-step tau / h^2 of the exp plan (persistent kernel)
     size_t tau_cap = 0;
+    // psi_1 on the persistent kernel: its plan (m a multiple of the kernel's K),
+    // per-step tau / h^2 and the sub-step factors c_j = e^{-i t mu j / S}
+    TaylorPlan plan_psi_p;
+    float *tau_psi_dev = nullptr;
+    float2 *wcoef_dev = nullptr;
+    size_t tau_psi_cap = 0, wcoef_cap = 0;
     unsigned *bar = nullptr;   // grid-barrier words of the persistent kernel
     // batched solves (several right-hand sides of this problem in lockstep)
     struct Rhs {
@@ -299,6 +305,8 @@ static void make_plans(mxp_problem *P)
     P->plan_exp = make_plan(P->nu, P->prm.exp_tol, theta_of(P), exp_fuse(P));
     P->plan_psi = make_plan(P->nu_aug, P->prm.exp_tol * 0.1, theta_of(P), effective_fuse(P));
     P->plan_psi2 = make_plan(P->nu_aug2, P->prm.exp_tol * 0.1, theta_of(P), effective_fuse(P));
+    if (P->persist_cfg >= 0)
+        P->plan_psi_p = make_plan(P->nu_aug, P->prm.exp_tol * 0.1, theta_of(P), persist2d_cfg_k(P->persist_cfg));
 }
 
 // Per-step tau / h^2 of the exp plan for the persistent kernel.
@@ -318,6 +326,32 @@ static mxp_status upload_tau(mxp_problem *P)
         P->tau_cap = cnt;
     }
     CK(cudaMemcpyAsync(P->tau_dev, tau.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, P->stream));
+    // the psi_1 plan: tau of every step and c_j = e^{-i t mu j / S}, j = 1 .. S-1
+    const TaylorPlan &pq = P->plan_psi_p;
+    const size_t cq = (size_t)pq.S * pq.m;
+    std::vector<float> tq(cq);
+    for (int sub = 0; sub < pq.S; ++sub)
+        for (int k = pq.m; k >= 1; --k)
+            tq[(size_t)sub * pq.m + (pq.m - k)] = (float)(P->prm.t / ((double)pq.S * k * h2));
+    std::vector<float2> wc((size_t)std::max(pq.S - 1, 1));
+    for (int j = 1; j < pq.S; ++j) {
+        const cd c = std::exp(cd(0.0, -P->prm.t * P->mu * j / pq.S));
+        wc[(size_t)j - 1] = make_float2((float)c.real(), (float)c.imag());
+    }
+    if (cq > P->tau_psi_cap) {
+        cudaFree(P->tau_psi_dev);
+        P->tau_psi_dev = nullptr;
+        CK(cudaMalloc(&P->tau_psi_dev, cq * sizeof(float)));
+        P->tau_psi_cap = cq;
+    }
+    if (wc.size() > P->wcoef_cap) {
+        cudaFree(P->wcoef_dev);
+        P->wcoef_dev = nullptr;
+        CK(cudaMalloc(&P->wcoef_dev, wc.size() * sizeof(float2)));
+        P->wcoef_cap = wc.size();
+    }
+    CK(cudaMemcpyAsync(P->tau_psi_dev, tq.data(), cq * sizeof(float), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->wcoef_dev, wc.data(), wc.size() * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
     CK(cudaStreamSynchronize(P->stream));
     return MXP_OK;
 }
@@ -895,6 +929,43 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
         launch_convert_out<S>(b[1], out, x, out_mode, n, st);
         P->passes += (int64_t)Ssub * m;
         return (int64_t)Ssub * m;
+    }
+    if (which == 1 && P->persist_cfg >= 0 && sizeof(S) <= 8 && P->plan_psi_p.S > 1 && P->tau_psi_dev) {
+        // psi_1 on the persistent kernel.  With u(tau) the solution of u' = M u + v
+        // shifted by e^{-i t mu tau}, one sub-step of length 1/S is
+        //   u_{j+1} = exp(M'/S) u_j + c_j w,  c_j = e^{-i t mu j / S},
+        // where w = u_1 (the first sub-step from u_0 = 0) does not depend on j.
+        // The first sub-step runs on the per-point sweep (augmented matrix), the
+        // other S - 1 in one persistent launch that adds c_j w after sub-step j.
+        const TaylorPlan &pq = P->plan_psi_p;
+        const int Kp = persist2d_cfg_k(P->persist_cfg);
+        const cd rotq(0.0, -t * P->mu / pq.S);
+        AugScalars augq(1, rotq, pq.S);
+        augq.begin_substep();
+        int in = 0;
+        for (int k = pq.m; k >= 1; --k) {
+            sc.sigma = PrecData<S>::c(cd(0.0, t / ((double)pq.S * k)));
+            sc.gamma = PrecData<S>::c(augq.gamma(k));
+            sc.rho = PrecData<S>::c(cd(1.0));
+            const int o = (in == 0) ? 1 : 3 - in;           // y = b[0] (zero) throughout
+            launch_step<S>(P->geom, PrecData<S>::coef(P), PrecData<S>::kappa(P), sc, b[in], b[0], vs, b[o], st);
+            augq.step(k);
+            in = o;
+        }
+        S *w = b[in];                                       // b[1] or b[2]
+        S *res = b[3 - in];
+        const cudaError_t ce = launch_persist2d<S>(
+            P->persist_cfg, P->geom, P->grid.npml, P->coef32s, P->kappa32, make_float2(1.0f, (float)P->prm.shift_s),
+            (float)(P->grid.h * P->grid.h), P->tau_psi_dev, (pq.S - 1) * pq.m / Kp, pq.m / Kp,
+            make_float2((float)final_rho.real(), (float)final_rho.imag()), P->bar, P->p_txo, P->p_tyo, P->p_ntx,
+            P->p_nty, w, b[0], vs, res, st, w, P->wcoef_dev);
+        if (ce != cudaSuccess) {
+            fail(MXP_ECUDA, std::string("persistent psi_1 kernel: ") + cudaGetErrorString(ce));
+            return -1;
+        }
+        launch_convert_out<S>(res, out, x, out_mode, n, st);
+        P->passes += (int64_t)pq.S * pq.m;
+        return (int64_t)pq.S * pq.m;
     }
     if (which == 0 && P->grid.dim == 3 && P->f3_cfg >= 0 && sizeof(S) <= 8 &&
         m % fused3d_cfg_k(P->f3_cfg) == 0) {
@@ -2072,6 +2143,8 @@ void mxp_destroy(mxp_problem *P)
     cudaFree(P->rt); cudaFree(P->tmp); cudaFree(P->tmp2); cudaFree(P->bdev); cudaFree(P->xdev);
     cudaFree(P->ks.partials);
     cudaFree(P->tau_dev);
+    cudaFree(P->tau_psi_dev);
+    cudaFree(P->wcoef_dev);
     cudaFree(P->bar);
     if (P->host_scal) cudaFreeHost(P->host_scal);
     free_arnoldi(P->inner);

@@ -31,6 +31,10 @@ struct PersistArgs {
     int npass, pass_per_sub;     // passes in total and per sub-step
     float2 rho;                  // e^{i t mu}: multiplies the result (undoes the shift)
     unsigned *bar;               // [0] arrival count, [1] generation, [2] error flag, [4..] tile epochs
+    // psi_1 by sub-steps (nullptr for exp): after sub-step j (1-based) the tile
+    // gains wcoef[j-1] * w (w in the storage type S)
+    const void *w;
+    const float2 *wcoef;
 };
 
 constexpr long long kBarrierSpinLimit = 1ll << 24;   // x >= 32 ns sleep: about a second
@@ -252,6 +256,20 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
             }
             __syncthreads();
         }
+        if (a.w && ((pass + 1) % a.pass_per_sub) == 0) {
+            // u_{j+1} = exp(h M') u_j + c_j w on the tile's own cells; the ring gets
+            // the same from the neighbours' strips
+            const float2 cj = a.wcoef[(pass + 1) / a.pass_per_sub - 1];
+            const S *w = static_cast<const S *>(a.w);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if ((tilemask >> r) & 1u) {
+                    const int ry = grp * R + r;
+                    float2 &cell = b0[(ry + 1) * PX + tx + 1];
+                    cell = cadd(cell, cmul(cj, St<S>::ld(w, (int64_t)(gy0 + ry) * n0 + gx)));
+                }
+            }
+        }
         if (pass == a.npass - 1) break;
         // publish the tile's edge strips, meet, pull the ring from the neighbours
         S *ex = (pass & 1) ? ex1 : ex0;
@@ -398,7 +416,8 @@ template <typename S>
 cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef, const float *kappa,
                              float2 zfac, float h2, const float *tau_dev, int npass,
                              int pass_per_sub, float2 rho, unsigned *bar, int txo, int tyo,
-                             int ntx, int nty, const S *x, S *ex0, S *ex1, S *out, cudaStream_t st)
+                             int ntx, int nty, const S *x, S *ex0, S *ex1, S *out, cudaStream_t st,
+                             const S *w, const float2 *wcoef)
 {
     void *fn;
     size_t smem;
@@ -421,6 +440,8 @@ cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef
     a.pass_per_sub = pass_per_sub;
     a.rho = rho;
     a.bar = bar;
+    a.w = w;
+    a.wcoef = wcoef;
     void *args[] = {&a, (void *)&x, (void *)&ex0, (void *)&ex1, (void *)&out};
     const PCfg c = kPCfgs[id];
     cudaError_t e = cudaMemsetAsync(bar, 0, (4 + (size_t)ntx * nty * kPersistFlagStride) * sizeof(unsigned), st);
@@ -451,7 +472,7 @@ cudaError_t barrier_selftest(unsigned *bar, cudaStream_t st)
     template cudaError_t launch_persist2d<S>(int, const Geom &, int, const float2 *, const float *, \
                                              float2, float, const float *, int, int, float2,  \
                                              unsigned *, int, int, int, int, const S *, S *,  \
-                                             S *, S *, cudaStream_t);
+                                             S *, S *, cudaStream_t, const S *, const float2 *);
 MXP_PINST(float2)
 MXP_PINST(__nv_bfloat162)
 #undef MXP_PINST

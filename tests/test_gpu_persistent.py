@@ -81,3 +81,40 @@ def test_persistent_refuses_grids_that_do_not_fit(native):
     G = native.Problem.from_grid(grid, c, p)
     G.set_params(prec="c64", exp_tol=1e-6, persist_cfg=0)
     assert G.persist_config()[0] == -1
+
+
+@pytest.mark.parametrize("grid", [I.Grid(2, (290, 157), 6), I.Grid(2, (64, 64), 10)])
+@pytest.mark.parametrize("prec", ["c64", "bf16s"])
+def test_persistent_psi1_matches_per_pass_and_oracle(native, grid, prec):
+    """psi_1 on the persistent kernel (first sub-step per point, the rest in one
+    launch adding c_j w after every sub-step) against the per-pass sweeps and the
+    oracle, for every configuration that fits; also the fixed-point operator
+    x - psi_1 x of the second inverse formula."""
+    c = I.layered_grf(grid, seed=43, corr_cells=3.0)
+    p = I.paper_params(grid, c, ppw=10.0)
+    P = oracle.Problem.from_grid(grid, c, p)
+    x = I.random_complex(grid.n_total, 21)
+    xd = torch.from_numpy(x).cuda()
+    G = native.Problem.from_grid(grid, c, p)
+    G.set_params(prec=prec, exp_tol=1e-6, fuse_k=1, persist_cfg=-2)
+    base = G.apply_phi(1, xd)[0].cpu().numpy()
+    ref = P.phi(1, x)[0]
+    bound = 2e-4 if prec == "c64" else 8e-2
+    ran = 0
+    for cfg in range(N_PCFG):
+        G.set_params(fuse_k=0, persist_cfg=cfg)
+        if G.persist_config()[0] != cfg:
+            continue
+        ran += 1
+        got = G.apply_phi(1, xd)[0].cpu().numpy()
+        assert _rel(got, ref) < bound, (cfg, _rel(got, ref))
+        if prec == "c64":
+            assert _rel(got, base) < 5e-5, (cfg, _rel(got, base))
+    assert ran >= 1
+    # the second inverse formula's apply runs psi_1 actions on this path
+    G.set_params(precond=2, inner_fixed=3, exp_tol=1e-6)
+    r = I.random_complex(grid.n_total, 22)
+    w_ref, it, _ = P.matexpre(r, fixed=3, variant=1)
+    w, st = G.apply_matexpre(torch.from_numpy(r).cuda())
+    assert st["inner_iters"] == 3
+    assert _rel(w.cpu().numpy(), w_ref) < (5e-4 if prec == "c64" else 2e-1)
