@@ -105,6 +105,7 @@ struct mxp_problem {
     int nfaces = 0;
     double2 *face64 = nullptr;
     float2 *face32 = nullptr;
+    float2 *face32s = nullptr;            // face32 scaled by h^2 (persistent kernel)
     int64_t face_off[6] = {0, 0, 0, 0, 0, 0};
     // tensor maps of the TMA-staged 3D sweep (built on first use per precision)
     Tma3Maps *tma3 = nullptr;
@@ -651,18 +652,32 @@ static mxp_status tune_fused(mxp_problem *P)
     return MXP_OK;
 }
 
+// Face terms of a 2D problem for the persistent kernel (h^2-scaled), or nullptr.
+struct PersistFaces {
+    const float2 *f[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+static PersistFaces persist_faces(const mxp_problem *P)
+{
+    PersistFaces pf;
+    if (P->nfaces && P->face32s)
+        for (int f = 0; f < 4; ++f)
+            if (P->bc[f] != MXP_BC_DIRICHLET) pf.f[f] = P->face32s + P->face_off[f];
+    return pf;
+}
+
 template <typename S>
 static cudaError_t persist_action(mxp_problem *P, const S *x, S *out)
 {
     const TaylorPlan &pl = P->plan_exp;
     const int K = persist2d_cfg_k(P->persist_cfg);
     const cd rho = std::exp(cd(0.0, P->prm.t * P->mu));
+    const PersistFaces pf = persist_faces(P);
     return launch_persist2d<S>(P->persist_cfg, P->geom, P->grid.npml, P->coef32s, P->kappa32,
                                make_float2(1.0f, (float)P->prm.shift_s),
                                (float)(P->grid.h * P->grid.h), P->tau_dev, pl.S * pl.m / K, pl.m / K,
                                make_float2((float)rho.real(), (float)rho.imag()), P->bar, P->p_txo,
                                P->p_tyo, P->p_ntx, P->p_nty, x, (S *)P->hb[2], (S *)P->hb[3], out,
-                               P->stream);
+                               P->stream, nullptr, nullptr, P->nfaces ? pf.f : nullptr);
 }
 
 // Try the persistent exp-action kernels: time one whole action of each
@@ -822,9 +837,17 @@ static mxp_status retune(mxp_problem *P)
     P->persist_cfg = -1;
     P->f3_cfg = -1;
     if (P->nfaces) {
-        // the tiled and persistent sweeps assume zero ghosts: faces keep the unfused sweep
+        // the tiled sweeps assume zero ghosts; in 2D the persistent kernel carries
+        // the face terms and is used whenever a configuration fits
         P->fused_cfg = -1;
+        P->fused_cost = 1e30;
         make_plans(P);
+        if (P->grid.dim == 2) {
+            if (P->prm.prec == MXP_C64) CKS(tune_persist<float2>(P, P->fused_cost));
+            else if (P->prm.prec == MXP_BF16S) CKS(tune_persist<__nv_bfloat162>(P, P->fused_cost));
+            make_plans(P);
+            if (P->persist_cfg >= 0) CKS(upload_tau(P));
+        }
         return MXP_OK;
     }
     if (P->grid.dim == 3) {
@@ -958,7 +981,7 @@ static int64_t phi_action(mxp_problem *P, int which, const double2 *x, double2 *
             P->persist_cfg, P->geom, P->grid.npml, P->coef32s, P->kappa32, make_float2(1.0f, (float)P->prm.shift_s),
             (float)(P->grid.h * P->grid.h), P->tau_psi_dev, (pq.S - 1) * pq.m / Kp, pq.m / Kp,
             make_float2((float)final_rho.real(), (float)final_rho.imag()), P->bar, P->p_txo, P->p_tyo, P->p_ntx,
-            P->p_nty, w, b[0], vs, res, st, w, P->wcoef_dev);
+            P->p_nty, w, b[0], vs, res, st, w, P->wcoef_dev, P->nfaces ? persist_faces(P).f : nullptr);
         if (ce != cudaSuccess) {
             fail(MXP_ECUDA, std::string("persistent psi_1 kernel: ") + cudaGetErrorString(ce));
             return -1;
@@ -1850,13 +1873,16 @@ static mxp_status build_faces(mxp_problem *P)
     }
     cudaFree(P->face64);
     cudaFree(P->face32);
+    cudaFree(P->face32s);
     P->face64 = nullptr;
     P->face32 = nullptr;
+    P->face32s = nullptr;
     if (total == 0) return MXP_OK;
     std::vector<double> c((size_t)P->ntot);
     CK(cudaMemcpy(c.data(), P->c_dev, (size_t)P->ntot * sizeof(double), cudaMemcpyDeviceToHost));
     std::vector<double2> f64((size_t)total);
-    std::vector<float2> f32((size_t)total);
+    std::vector<float2> f32((size_t)total), f32s((size_t)total);
+    const double h2 = P->grid.h * P->grid.h;
     const double h = P->grid.h, omega = P->prm.omega;
     for (int f = 0; f < 2 * dim; ++f) {
         if (P->bc[f] == MXP_BC_DIRICHLET) continue;
@@ -1884,12 +1910,15 @@ static mxp_status build_faces(mxp_problem *P)
                 const size_t o = (size_t)(P->face_off[f] + u0 + (int64_t)m0 * u1);
                 f64[o] = make_double2(term.real(), term.imag());
                 f32[o] = make_float2((float)term.real(), (float)term.imag());
+                f32s[o] = make_float2((float)(term.real() * h2), (float)(term.imag() * h2));
             }
     }
     CK(cudaMalloc(&P->face64, (size_t)total * sizeof(double2)));
     CK(cudaMalloc(&P->face32, (size_t)total * sizeof(float2)));
+    CK(cudaMalloc(&P->face32s, (size_t)total * sizeof(float2)));
     CK(cudaMemcpyAsync(P->face64, f64.data(), (size_t)total * sizeof(double2), cudaMemcpyHostToDevice, P->stream));
     CK(cudaMemcpyAsync(P->face32, f32.data(), (size_t)total * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->face32s, f32s.data(), (size_t)total * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
     CK(cudaStreamSynchronize(P->stream));
     return MXP_OK;
 }
@@ -2137,7 +2166,7 @@ void mxp_destroy(mxp_problem *P)
     cudaStreamSynchronize(P->stream);
     cudaFree(P->c_dev); cudaFree(P->kappa64); cudaFree(P->kappa32);
     cudaFree(P->coef64); cudaFree(P->coef32); cudaFree(P->coef32s);
-    cudaFree(P->face64); cudaFree(P->face32);
+    cudaFree(P->face64); cudaFree(P->face32); cudaFree(P->face32s);
     for (int i = 0; i < 4; ++i) cudaFree(P->hb[i]);
     tma3_destroy(P->tma3);
     cudaFree(P->rt); cudaFree(P->tmp); cudaFree(P->tmp2); cudaFree(P->bdev); cudaFree(P->xdev);

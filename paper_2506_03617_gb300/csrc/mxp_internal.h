@@ -152,7 +152,8 @@ cudaError_t launch_persist2d(int cfg, const Geom &g, int npml, const float2 *coe
                              float2 zfac, float h2, const float *tau_dev, int npass,
                              int pass_per_sub, float2 rho, unsigned *bar, int txo, int tyo,
                              int ntx, int nty, const S *x, S *ex0, S *ex1, S *out, cudaStream_t st,
-                             const S *w = nullptr, const float2 *wcoef = nullptr);
+                             const S *w = nullptr, const float2 *wcoef = nullptr,
+                             const float2 *const *faces = nullptr);
 
 // Runs the bounded grid barrier with an arrival count that is never reached.
 cudaError_t barrier_selftest(unsigned *bar, cudaStream_t st);

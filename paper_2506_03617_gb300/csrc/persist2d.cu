@@ -35,6 +35,10 @@ struct PersistArgs {
     // gains wcoef[j-1] * w (w in the storage type S)
     const void *w;
     const float2 *wcoef;
+    // ghost-point faces x-, x+, y-, y+ (nullptr = zero Dirichlet): diagonal term
+    // of each boundary cell, scaled by h^2, indexed by the position along the face
+    const float2 *face[4];
+    int nfaces;
 };
 
 constexpr long long kBarrierSpinLimit = 1ll << 24;   // x >= 32 ns sleep: about a second
@@ -169,11 +173,16 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
     unsigned inmask = 0u;     // point inside the grid and the region
     unsigned tilemask = 0u;   // point inside this CTA's tile
     unsigned stripmask = 0u;  // tile point within K of the tile edge (published)
+    unsigned facemask = 0u;   // point on a sound-hard or absorbing face of the grid
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int ry = grp * R + r;
         const int gy = gy0 + ry;
         const bool in = inx && ry < RH && gy >= 0 && gy < n1;
+        if (in && a.nfaces &&
+            ((a.face[0] && gx == 0) || (a.face[1] && gx == n0 - 1) || (a.face[2] && gy == 0) ||
+             (a.face[3] && gy == n1 - 1)))
+            facemask |= 1u << r;
         const int64_t q = in ? (int64_t)gy * n0 + gx : 0;
         const float2 p0 = St<S>::ld(x, q);
         ks[ry * BX + tx] = a.kappa[q];
@@ -252,6 +261,24 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
                 for (int j = 0; j < CH; ++j) {
                     const int ry = r0 + c + j;
                     if ((inmask >> (c + j)) & 1u) dst[(ry + 1) * PX + tx + 1] = o[j];
+                }
+            }
+            if (facemask) {
+                // boundary rows of a ghost-point face: the ghost is a multiple of the
+                // row's own unknown, so q gains face * p (added to this thread's cells)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if ((facemask >> r) & 1u) {
+                        const int ry = r0 + r, gy = gy0 + ry;
+                        float2 f = make_float2(0.f, 0.f);
+                        if (a.face[0] && gx == 0) f = cadd(f, a.face[0][gy]);
+                        if (a.face[1] && gx == n0 - 1) f = cadd(f, a.face[1][gy]);
+                        if (a.face[2] && gy == 0) f = cadd(f, a.face[2][gx]);
+                        if (a.face[3] && gy == n1 - 1) f = cadd(f, a.face[3][gx]);
+                        const float2 fp = cmul(f, src[(ry + 1) * PX + tx + 1]);
+                        float2 &cell = dst[(ry + 1) * PX + tx + 1];
+                        cell = make_float2(fmaf(-tau, fp.y, cell.x), fmaf(tau, fp.x, cell.y));
+                    }
                 }
             }
             __syncthreads();
@@ -417,7 +444,7 @@ cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef
                              float2 zfac, float h2, const float *tau_dev, int npass,
                              int pass_per_sub, float2 rho, unsigned *bar, int txo, int tyo,
                              int ntx, int nty, const S *x, S *ex0, S *ex1, S *out, cudaStream_t st,
-                             const S *w, const float2 *wcoef)
+                             const S *w, const float2 *wcoef, const float2 *const *faces)
 {
     void *fn;
     size_t smem;
@@ -442,6 +469,11 @@ cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef
     a.bar = bar;
     a.w = w;
     a.wcoef = wcoef;
+    a.nfaces = 0;
+    for (int f = 0; f < 4; ++f) {
+        a.face[f] = faces ? faces[f] : nullptr;
+        a.nfaces += (a.face[f] != nullptr);
+    }
     void *args[] = {&a, (void *)&x, (void *)&ex0, (void *)&ex1, (void *)&out};
     const PCfg c = kPCfgs[id];
     cudaError_t e = cudaMemsetAsync(bar, 0, (4 + (size_t)ntx * nty * kPersistFlagStride) * sizeof(unsigned), st);
@@ -472,7 +504,8 @@ cudaError_t barrier_selftest(unsigned *bar, cudaStream_t st)
     template cudaError_t launch_persist2d<S>(int, const Geom &, int, const float2 *, const float *, \
                                              float2, float, const float *, int, int, float2,  \
                                              unsigned *, int, int, int, int, const S *, S *,  \
-                                             S *, S *, cudaStream_t, const S *, const float2 *);
+                                             S *, S *, cudaStream_t, const S *, const float2 *, \
+                                             const float2 *const *);
 MXP_PINST(float2)
 MXP_PINST(__nv_bfloat162)
 #undef MXP_PINST

@@ -69,14 +69,32 @@ def test_phi_parity_with_faces_c128(native, name, grid, bc, which):
 
 @pytest.mark.parametrize("prec,bound", [("c64", 2e-4), ("bf16s", 8e-2)])
 def test_low_precision_phi_with_faces(native, prec, bound):
+    """Faces run on the per-point sweep and on the persistent kernel (which adds
+    the face term to the boundary rows after each step), never on the tiles."""
     grid, bc = CASES[0][1], CASES[0][2]
-    P, G, _, _ = _pair(native, grid, bc, prec=prec, exp_tol=1e-6)
-    assert G.tile_config()[0] == -1 and G.persist_config()[0] == -1   # faces keep the unfused sweep
+    P, G, _, _ = _pair(native, grid, bc, prec=prec, exp_tol=1e-6, persist_cfg=-2)
+    assert G.tile_config()[0] == -1 and G.persist_config()[0] == -1
     x = I.random_complex(grid.n_total, 3)
+    base = {}
     for which in (0, 1):
         ref, _ = P.phi(which, x)
         got, _ = G.apply_phi(which, _cuda(x))
-        assert _rel(got.cpu().numpy(), ref) < bound
+        base[which] = got.cpu().numpy()
+        assert _rel(base[which], ref) < bound
+    ran = 0
+    for cfg in range(6):
+        G.set_params(persist_cfg=cfg)
+        if G.persist_config()[0] != cfg:
+            continue
+        ran += 1
+        assert G.tile_config()[0] == -1 and G.sweep_kernel() == "persistent_2d"
+        for which in (0, 1):
+            ref, _ = P.phi(which, x)
+            got = G.apply_phi(which, _cuda(x))[0].cpu().numpy()
+            assert _rel(got, ref) < bound, (cfg, which, _rel(got, ref))
+            if prec == "c64":
+                assert _rel(got, base[which]) < 5e-5, (cfg, which)
+    assert ran >= 1
 
 
 def test_matexpre_fixed_trip_parity_with_faces(native):
