@@ -2,8 +2,9 @@
 // operator of Eq. helmholtz, Eq. pml-1d-s and Sec. 3.4) with the planes staged
 // in shared memory by the Tensor Memory Accelerator.
 //
-// A block owns a 32 x 8 column of the grid over a segment of planes and marches
-// along z.  Plane z of p (the tile plus a halo), of y, of kappa and of v is
+// A block of 32 x 8 threads owns a 32 x 16 column of the grid (two rows per
+// thread, which halves the per-plane barriers and waits per point) over a
+// segment of planes and marches along z.  Plane z of p (the tile plus a halo), of y, of kappa and of v is
 // brought into one stage of a ring in shared memory by cp.async.bulk.tensor
 // loads that one thread issues several planes ahead; an mbarrier per stage
 // counts the bytes that arrived.  The step at plane z then reads p(z-1), p(z),
@@ -32,10 +33,14 @@
 #ifndef MXP_TMA3_STAGES
 #define MXP_TMA3_STAGES 6
 #endif
+#ifndef MXP_TMA3_RPT
+#define MXP_TMA3_RPT 2
+#endif
 
 namespace mxp {
 
-constexpr int kTX = 32, kTY = 8;          // tile of a block
+constexpr int kRPT = MXP_TMA3_RPT;        // rows of the tile per thread
+constexpr int kTX = 32, kTY = 8 * kRPT;   // tile of a block (32 x 8 threads)
 constexpr int kStages = MXP_TMA3_STAGES;  // planes resident or in flight per block
 constexpr long long kTmaPollLimit = 1ll << 22;
 
@@ -111,7 +116,7 @@ __device__ __forceinline__ typename St<S>::C sm_ld(const S *p, int i)
 }
 
 template <typename S, bool HAS_Y, bool HAS_V>
-__global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename St<S>::C *__restrict__ coef,
+__global__ void __launch_bounds__(kTX * 8) k_step3z_tma(Geom g, const typename St<S>::C *__restrict__ coef,
                                                          StepScalars<typename St<S>::C> sc,
                                                          const __grid_constant__ CUtensorMap mp,
                                                          const __grid_constant__ CUtensorMap my,
@@ -135,8 +140,7 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2], nm = g.nmax;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int z0 = blockIdx.z * lz, z1 = min(z0 + lz, n2);
-    const int i = x0 + tx, j = y0 + ty;
-    const bool active = i < n0 && j < n1;
+    const int i = x0 + tx;          // rows of this thread: y0 + ty + 8 rr, rr < kRPT
     const int nplanes = z1 - z0 + 2;          // planes z0-1 .. z1
 
     // byte offsets of the parts of a stage
@@ -173,18 +177,22 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
     }
 
     // per-column coefficients (constant along z)
-    C wpx = czero3<C>(), wmx = wpx, wcx = wpx, wpy = wpx, wmy = wpx, wcy = wpx;
-    if (active) {
-        wpx = coef[i]; wmx = coef[nm + i]; wcx = coef[2 * nm + i];
-        wpy = coef[3 * nm + j]; wmy = coef[4 * nm + j]; wcy = coef[5 * nm + j];
-    }
     const C *cz = coef + 6 * nm;
     const int p0 = g.npml;
-    const bool xyin = g.fast && i >= p0 && i < n0 - p0 && j >= p0 && j < n1 - p0;
-    const int cidx = (ty + 1) * PW + tx + HL;
-    const int tidx = ty * kTX + tx;
+    C wpx = czero3<C>(), wmx = wpx, wcx = wpx;
+    if (i < n0) { wpx = coef[i]; wmx = coef[nm + i]; wcx = coef[2 * nm + i]; }
+    C wpy[kRPT], wmy[kRPT], wcy[kRPT];
+    bool active[kRPT], xyin[kRPT];
+#pragma unroll
+    for (int rr = 0; rr < kRPT; ++rr) {
+        const int j = y0 + ty + 8 * rr;
+        active[rr] = i < n0 && j < n1;
+        wpy[rr] = wmy[rr] = wcy[rr] = czero3<C>();
+        if (active[rr]) { wpy[rr] = coef[3 * nm + j]; wmy[rr] = coef[4 * nm + j]; wcy[rr] = coef[5 * nm + j]; }
+        xyin[rr] = g.fast && i >= p0 && i < n0 - p0 && j >= p0 && j < n1 - p0;
+    }
     int sm_ = 0, sc_ = 1, sp_ = 2;            // stages of planes pi - 1, pi, pi + 1
-    S *outp = pout + (i + g.s1 * j + g.s2 * z0);
+    S *outp = pout + (i + g.s1 * (y0 + ty) + g.s2 * z0);
     // z-axis coefficients of the current plane, loaded one plane ahead
     C czp = cz[z0], czm = cz[nm + z0], czc = cz[2 * nm + z0];
 
@@ -209,35 +217,41 @@ __global__ void __launch_bounds__(kTX *kTY) k_step3z_tma(Geom g, const typename 
         if (s_fail) break;
         const int kn = (k + 1 < n2) ? k + 1 : k;
         const C czp_n = cz[kn], czm_n = cz[nm + kn], czc_n = cz[2 * nm + kn];
-        if (active) {
+        {
             const unsigned char *bc = stg + sc_ * SB;
             const S *pc_ = reinterpret_cast<const S *>(bc);
             const S *pm_ = reinterpret_cast<const S *>(stg + sm_ * SB);
             const S *pp_ = reinterpret_cast<const S *>(stg + sp_ * SB);
-            const C pc = sm_ld<S>(pc_, cidx);
-            const C xp = sm_ld<S>(pc_, cidx + 1), xm = sm_ld<S>(pc_, cidx - 1);
-            const C yp = sm_ld<S>(pc_, cidx + PW), ym = sm_ld<S>(pc_, cidx - PW);
-            const C pp = sm_ld<S>(pp_, cidx), pm = sm_ld<S>(pm_, cidx);
-            const bool inner = xyin && k >= p0 && k < n2 - p0;
-            C acc;
-            if (inner) {
-                acc = cadd(cadd(cadd(xp, xm), cadd(yp, ym)), cadd(pp, pm));
-                const R s = (R)g.ih2;
-                acc = CT<C>::mk(acc.x * s, acc.y * s);
-            } else {
-                acc = cadd(cmul(wpx, xp), cmul(wmx, xm));
-                acc = cadd(acc, cadd(cmul(wpy, yp), cmul(wmy, ym)));
-                acc = cadd(acc, cadd(cmul(czp, pp), cmul(czm, pm)));
+#pragma unroll
+            for (int rr = 0; rr < kRPT; ++rr) {
+                if (!active[rr]) continue;
+                const int cidx = (ty + 8 * rr + 1) * PW + tx + HL;
+                const int tidx = (ty + 8 * rr) * kTX + tx;
+                const C pc = sm_ld<S>(pc_, cidx);
+                const C xp = sm_ld<S>(pc_, cidx + 1), xm = sm_ld<S>(pc_, cidx - 1);
+                const C yp = sm_ld<S>(pc_, cidx + PW), ym = sm_ld<S>(pc_, cidx - PW);
+                const C pp = sm_ld<S>(pp_, cidx), pm = sm_ld<S>(pm_, cidx);
+                const bool inner = xyin[rr] && k >= p0 && k < n2 - p0;
+                C acc;
+                if (inner) {
+                    acc = cadd(cadd(cadd(xp, xm), cadd(yp, ym)), cadd(pp, pm));
+                    const R s = (R)g.ih2;
+                    acc = CT<C>::mk(acc.x * s, acc.y * s);
+                } else {
+                    acc = cadd(cmul(wpx, xp), cmul(wmx, xm));
+                    acc = cadd(acc, cadd(cmul(wpy[rr], yp), cmul(wmy[rr], ym)));
+                    acc = cadd(acc, cadd(cmul(czp, pp), cmul(czm, pm)));
+                }
+                const C wcs = cadd(cadd(wcx, wcy[rr]), czc);
+                const R kp = reinterpret_cast<const float *>(bc + OK)[tidx];
+                const C diag = CT<C>::mk(kp * sc.zfac.x - sc.mu - wcs.x, kp * sc.zfac.y - wcs.y);
+                acc = cadd(acc, cmul(diag, pc));
+                C out = cmul(sc.sigma, acc);
+                if (HAS_Y) out = cadd(out, sm_ld<S>(reinterpret_cast<const S *>(bc + OY), tidx));
+                if (HAS_V) out = cadd(out, cmul(sc.gamma, sm_ld<S>(reinterpret_cast<const S *>(bc + OV), tidx)));
+                out = cmul(sc.rho, out);
+                St<S>::st(outp, g.s1 * 8 * rr, out);
             }
-            const C wcs = cadd(cadd(wcx, wcy), czc);
-            const R kp = reinterpret_cast<const float *>(bc + OK)[tidx];
-            const C diag = CT<C>::mk(kp * sc.zfac.x - sc.mu - wcs.x, kp * sc.zfac.y - wcs.y);
-            acc = cadd(acc, cmul(diag, pc));
-            C out = cmul(sc.sigma, acc);
-            if (HAS_Y) out = cadd(out, sm_ld<S>(reinterpret_cast<const S *>(bc + OY), tidx));
-            if (HAS_V) out = cadd(out, cmul(sc.gamma, sm_ld<S>(reinterpret_cast<const S *>(bc + OV), tidx)));
-            out = cmul(sc.rho, out);
-            St<S>::st(outp, 0, out);
         }
         __syncthreads();                      // stage of plane pi - 1 is free
         if (tid == 0 && issued < nplanes) {
@@ -343,7 +357,7 @@ static cudaError_t launch3t(const Geom &g, const typename St<S>::C *coef, const 
     if (lz < 8) lz = 8;
     dim3 grid((g.n[0] + kTX - 1) / kTX, (g.n[1] + kTY - 1) / kTY, (g.n[2] + lz - 1) / lz);
     count_launch();
-    k_step3z_tma<S, HAS_Y, HAS_V><<<grid, dim3(kTX, kTY), smem, st>>>(g, coef, sc, t.p[ip], t.y[iy], t.k,
+    k_step3z_tma<S, HAS_Y, HAS_V><<<grid, dim3(kTX, 8), smem, st>>>(g, coef, sc, t.p[ip], t.y[iy], t.k,
                                                                       t.y[iv < 0 ? 0 : iv], pout, lz, err);
     return cudaGetLastError();
 }
