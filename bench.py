@@ -64,7 +64,7 @@ def parse_args():
                     help="parse an ncu --csv --print-units base log of dram__bytes_read/write.sum "
                          "for KERNEL (persist2d, fused2d or horner_step) and store the DRAM bytes per "
                          "launch with the kernel source hash in profiles/traffic.json; then exit")
-    ap.add_argument("--experiment", choices=["precond", "marmousi", "fused3d"], default=None,
+    ap.add_argument("--experiment", choices=["precond", "marmousi", "fused3d", "solve3d"], default=None,
                     help="run one of the side measurements (one JSON line per case) and exit: "
                          "precond = Algorithm 1 vs P_N vs the psi_2 variant on the 1088^2 "
                          "workload; marmousi = mixed boundary conditions on a Marmousi-shaped "
@@ -575,6 +575,17 @@ def run_experiment(args):
                               "inner_per_outer": row["inner_total"] / max(row["outer"], 1),
                               **row}), flush=True)
             prob.close()
+    elif args.experiment == "solve3d":
+        # converging-lens medium of Sec. 4 on 128^3 + 16 PML, point-like source at the centre
+        g, c, p = I.config_3d_lens(n_interior=128, npml=16)
+        b = torch.from_numpy(I.rhs_from_source(I.gaussian_source(g)).ravel()).cuda()
+        prob = N.Problem.from_grid(g, c, p)
+        for pr in ("c64", "bf16s"):
+            prob.set_params(prec=pr, exp_tol=1e-6)
+            _timed_solve(prob, b, maxit=2)
+            row = _timed_solve(prob, b, maxit=400)
+            print(json.dumps({"experiment": "solve3d", "workload": "3d_lens_160", "prec": pr,
+                              "kernel": prob.sweep_kernel(), "unknowns": g.n_total, **row}), flush=True)
     else:
         g, c, p = I.config_3d_homogeneous()
         prob = N.Problem.from_grid(g, c, p)
