@@ -698,6 +698,7 @@ static mxp_status tune_persist(mxp_problem *P, double best_cost)
     for (int id = 0; id < persist2d_num_cfgs(); ++id) {
         if (forced && id != P->prm.persist_cfg) continue;
         if (!forced && P->prm.fuse_k > 1 && persist2d_cfg_k(id) != P->prm.fuse_k) continue;
+        if (P->nfaces && !persist2d_cfg_faces(id)) continue;
         int txo, tyo, ntx, nty;
         if (!persist2d_plan<S>(id, P->geom.n[0], P->geom.n[1], P->device, &txo, &tyo, &ntx, &nty)) continue;
         P->persist_cfg = id;

@@ -348,18 +348,271 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
     }
 }
 
+// The same exp / psi_1 action with two adjacent columns per thread.  The east
+// neighbour of the first column and the west neighbour of the second are the
+// other column's centre (registers), the row below comes as one 16-byte load
+// for both, and kappa of both as one 8-byte load: about half the shared loads
+// per point of k_persist2d.  Cells outside the grid start at zero, have y = 0
+// and meet only zero coefficients, so they stay exactly zero and every row pair
+// is stored unmasked; cells past the region's edge only spread garbage inward
+// by one cell per step, which the K-cell ring absorbs.  No ghost-point faces.
+template <typename S, int K, int BXH, int BG, int R, int CH>
+__global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, const S *__restrict__ x,
+                                                             S *__restrict__ ex0,
+                                                             S *__restrict__ ex1,
+                                                             S *__restrict__ out)
+{
+    static_assert(K % 2 == 0, "K must be even: each pass starts and ends in buffer 0");
+    static_assert(R % CH == 0, "rows per thread must be a multiple of the chunk");
+    constexpr int BX = 2 * BXH;                 // region columns
+    constexpr int PX = BX + 4;                  // padded row: cell (ry, cx) at (ry + 1) PX + cx + 2
+    constexpr int PY = BG * R + 2;
+    extern __shared__ __align__(16) float2 sm[];
+    float2 *b0 = sm;
+    float2 *b1 = sm + PY * PX;
+    float2 *cy = b1 + PY * PX;                  // [BG*R][3] y-axis coefficients wp, wm, wc
+    float2 *ks = cy + 3 * BG * R;               // [BG*R][BXH] kappa of the column pair
+
+    const int tx = threadIdx.x % BXH;
+    const int grp = threadIdx.x / BXH;
+    const int bx = blockIdx.x % a.ntx, by = blockIdx.x / a.ntx;
+    const int RW = a.txo + 2 * K, RH = a.tyo + 2 * K;
+    const int gx0 = bx * a.txo - K, gy0 = by * a.tyo - K;
+    const int cx0 = 2 * tx;                     // region column of the first cell
+    const int n0 = a.n0, n1 = a.n1, nm = a.nmax;
+    const float h2 = a.h2;
+    int gx[2];
+    bool inx[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        gx[l] = gx0 + cx0 + l;
+        inx[l] = cx0 + l < RW && gx[l] >= 0 && gx[l] < n0;
+    }
+
+    for (int i = threadIdx.x; i < 2 * PY * PX; i += BXH * BG) sm[i] = make_float2(0.f, 0.f);
+    for (int r = threadIdx.x; r < BG * R; r += BXH * BG) {
+        const int gy = gy0 + r;
+        float2 wp = make_float2(0.f, 0.f), wm = make_float2(0.f, 0.f), wc = make_float2(0.f, 0.f);
+        if (gy >= 0 && gy < n1) {
+            wp = a.coef[3 * nm + gy];
+            wm = a.coef[4 * nm + gy];
+            wc = a.coef[5 * nm + gy];
+        }
+        cy[3 * r] = wp;
+        cy[3 * r + 1] = wm;
+        cy[3 * r + 2] = wc;
+    }
+    float2 wpx[2], wmx[2], wcx[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        wpx[l] = wmx[l] = wcx[l] = make_float2(0.f, 0.f);
+        if (inx[l]) {
+            wpx[l] = a.coef[gx[l]];
+            wmx[l] = a.coef[nm + gx[l]];
+            wcx[l] = a.coef[2 * nm + gx[l]];
+        }
+    }
+    const float2 zh = make_float2(a.zfac.x * h2, a.zfac.y * h2);
+    __syncthreads();
+
+    float2 y0r[R], y1r[R];
+    unsigned inmask[2] = {0u, 0u}, tilemask[2] = {0u, 0u}, stripmask[2] = {0u, 0u};
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int ry = grp * R + r;
+        const int gy = gy0 + ry;
+        float kap[2];
+        float2 pv[2];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const bool in = inx[l] && ry < RH && gy >= 0 && gy < n1;
+            const int64_t q = in ? (int64_t)gy * n0 + gx[l] : 0;
+            pv[l] = in ? St<S>::ld(x, q) : make_float2(0.f, 0.f);
+            kap[l] = a.kappa[q];
+            if (in) {
+                inmask[l] |= 1u << r;
+                b0[(ry + 1) * PX + cx0 + l + 2] = pv[l];
+                const int cx = cx0 + l;
+                const bool intile = cx >= K && cx < K + a.txo && ry >= K && ry < K + a.tyo;
+                if (intile) {
+                    tilemask[l] |= 1u << r;
+                    if (cx < 2 * K || cx >= a.txo || ry < 2 * K || ry >= a.tyo) stripmask[l] |= 1u << r;
+                }
+            }
+        }
+        ks[ry * BXH + tx] = make_float2(kap[0], kap[1]);
+        y0r[r] = pv[0];
+        y1r[r] = pv[1];
+    }
+    __syncthreads();
+
+    bool alive = true;
+    for (int pass = 0; pass < a.npass && alive; ++pass) {
+#pragma unroll 1
+        for (int s = 0; s < K; ++s) {
+            const float2 *src = (s & 1) ? b1 : b0;
+            float2 *dst = (s & 1) ? b0 : b1;
+            const float tau = a.tau[pass * K + s];
+            const int r0 = grp * R;
+            float4 up = *reinterpret_cast<const float4 *>(src + r0 * PX + cx0 + 2);
+            float4 cen = *reinterpret_cast<const float4 *>(src + (r0 + 1) * PX + cx0 + 2);
+#pragma unroll
+            for (int c = 0; c < R; c += CH) {
+                if (r0 + c >= RH) break;
+                float4 dn[CH];
+                float2 wl[CH], er[CH], kk[CH];
+                float4 o[CH];
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    const int ry = r0 + c + j;
+                    dn[j] = *reinterpret_cast<const float4 *>(src + (ry + 2) * PX + cx0 + 2);
+                    wl[j] = src[(ry + 1) * PX + cx0 + 1];
+                    er[j] = src[(ry + 1) * PX + cx0 + 4];
+                    kk[j] = ks[ry * BXH + tx];
+                }
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    const int ry = r0 + c + j;
+                    const float2 wpy = cy[3 * ry], wmy = cy[3 * ry + 1], wcy = cy[3 * ry + 2];
+                    const float2 cA = make_float2(cen.x, cen.y), cB = make_float2(cen.z, cen.w);
+                    const float2 uA = make_float2(up.x, up.y), uB = make_float2(up.z, up.w);
+                    const float2 nA = make_float2(dn[j].x, dn[j].y), nB = make_float2(dn[j].z, dn[j].w);
+                    float2 res[2];
+#pragma unroll
+                    for (int l = 0; l < 2; ++l) {
+                        const float2 e_ = l ? er[j] : cB, w_ = l ? cA : wl[j];
+                        const float2 n_ = l ? nB : nA, u_ = l ? uB : uA, c_ = l ? cB : cA;
+                        const float kv = l ? kk[j].y : kk[j].x;
+                        const float dx = fmaf(kv, zh.x, -(wcx[l].x + wcy.x));
+                        const float dy = fmaf(kv, zh.y, -(wcx[l].y + wcy.y));
+                        float qx = wpx[l].x * e_.x;
+                        qx = fmaf(-wpx[l].y, e_.y, qx);
+                        qx = fmaf(wmx[l].x, w_.x, qx);
+                        qx = fmaf(-wmx[l].y, w_.y, qx);
+                        qx = fmaf(wpy.x, n_.x, qx);
+                        qx = fmaf(-wpy.y, n_.y, qx);
+                        qx = fmaf(wmy.x, u_.x, qx);
+                        qx = fmaf(-wmy.y, u_.y, qx);
+                        qx = fmaf(dx, c_.x, qx);
+                        qx = fmaf(-dy, c_.y, qx);
+                        float qy = wpx[l].x * e_.y;
+                        qy = fmaf(wpx[l].y, e_.x, qy);
+                        qy = fmaf(wmx[l].x, w_.y, qy);
+                        qy = fmaf(wmx[l].y, w_.x, qy);
+                        qy = fmaf(wpy.x, n_.y, qy);
+                        qy = fmaf(wpy.y, n_.x, qy);
+                        qy = fmaf(wmy.x, u_.y, qy);
+                        qy = fmaf(wmy.y, u_.x, qy);
+                        qy = fmaf(dx, c_.y, qy);
+                        qy = fmaf(dy, c_.x, qy);
+                        const float2 yv = l ? y1r[c + j] : y0r[c + j];
+                        res[l] = make_float2(fmaf(-tau, qy, yv.x), fmaf(tau, qx, yv.y));
+                    }
+                    o[j] = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
+                    up = cen;
+                    cen = dn[j];
+                }
+#pragma unroll
+                for (int j = 0; j < CH; ++j)
+                    *reinterpret_cast<float4 *>(dst + (r0 + c + j + 1) * PX + cx0 + 2) = o[j];
+            }
+            __syncthreads();
+        }
+        if (a.w && ((pass + 1) % a.pass_per_sub) == 0) {
+            const float2 cj = a.wcoef[(pass + 1) / a.pass_per_sub - 1];
+            const S *w = static_cast<const S *>(a.w);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int ry = grp * R + r;
+#pragma unroll
+                for (int l = 0; l < 2; ++l)
+                    if ((tilemask[l] >> r) & 1u) {
+                        float2 &cell = b0[(ry + 1) * PX + cx0 + l + 2];
+                        cell = cadd(cell, cmul(cj, St<S>::ld(w, (int64_t)(gy0 + ry) * n0 + gx[l])));
+                    }
+            }
+        }
+        if (pass == a.npass - 1) break;
+        S *ex = (pass & 1) ? ex1 : ex0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int ry = grp * R + r;
+#pragma unroll
+            for (int l = 0; l < 2; ++l)
+                if ((stripmask[l] >> r) & 1u)
+                    St<S>::st(ex, (int64_t)(gy0 + ry) * n0 + gx[l], b0[(ry + 1) * PX + cx0 + l + 2]);
+        }
+        alive = neighbour_sync(a.bar, bx, by, a.ntx, a.nty, (unsigned)(pass + 1));
+        if (!alive) break;
+        const bool sub_end = ((pass + 1) % a.pass_per_sub) == 0;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const unsigned ring = inmask[l] & ~tilemask[l];
+            if (ring) {
+                float2 rv[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int ry = grp * R + r;
+                    const int64_t q = ((ring >> r) & 1u) ? (int64_t)(gy0 + ry) * n0 + gx[l] : 0;
+                    if (sizeof(S) == 8) {
+                        rv[r] = __ldcg(reinterpret_cast<const float2 *>(ex) + q);
+                    } else {
+                        const unsigned u = __ldcg(reinterpret_cast<const unsigned *>(ex) + q);
+                        rv[r] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if ((ring >> r) & 1u) b0[(grp * R + r + 1) * PX + cx0 + l + 2] = rv[r];
+            }
+        }
+        __syncthreads();
+        if (sub_end) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int ry = grp * R + r;
+                if ((inmask[0] >> r) & 1u) y0r[r] = b0[(ry + 1) * PX + cx0 + 2];
+                if ((inmask[1] >> r) & 1u) y1r[r] = b0[(ry + 1) * PX + cx0 + 3];
+            }
+        }
+    }
+    if (alive) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int ry = grp * R + r;
+#pragma unroll
+            for (int l = 0; l < 2; ++l)
+                if ((tilemask[l] >> r) & 1u)
+                    St<S>::st(out, (int64_t)(gy0 + ry) * n0 + gx[l], cmul(a.rho, b0[(ry + 1) * PX + cx0 + l + 2]));
+        }
+    }
+}
+
 struct PCfg {
     int K, BX, BG, R;
+    int x2;          // 1: two columns per thread (k_persist2d_x2, BX / 2 threads per row group)
 };
-static const PCfg kPCfgs[] = {{2, 128, 4, 18}, {4, 96, 4, 28}, {4, 96, 8, 14}, {4, 96, 9, 12},
-                               {2, 128, 8, 10}, {6, 96, 4, 28}};
+static const PCfg kPCfgs[] = {{2, 128, 4, 18, 0}, {4, 96, 4, 28, 0}, {4, 96, 8, 14, 0}, {4, 96, 9, 12, 0},
+                               {2, 128, 8, 10, 0}, {6, 96, 4, 28, 0}, {6, 96, 8, 14, 1}, {4, 96, 8, 14, 1}};
 constexpr int kNumP = sizeof(kPCfgs) / sizeof(kPCfgs[0]);
 
 int persist2d_num_cfgs() { return kNumP; }
 int persist2d_cfg_k(int id) { return kPCfgs[id].K; }
+bool persist2d_cfg_faces(int id) { return id >= 0 && id < kNumP && !kPCfgs[id].x2; }
+static int cfg_threads(const PCfg &c) { return c.x2 ? c.BX / 2 * c.BG : c.BX * c.BG; }
 
 template <typename S, int K, int BX, int BG, int R>
 static void *kernel_ptr() { return (void *)k_persist2d<S, K, BX, BG, R, (R % 4 == 0) ? 4 : 2>; }
+
+template <typename S, int K, int BX, int BG, int R>
+static void *kernel_ptr_x2() { return (void *)k_persist2d_x2<S, K, BX / 2, BG, R, (R % 4 == 0) ? 4 : 2>; }
+
+template <typename S, int K, int BX, int BG, int R>
+static size_t smem_bytes_x2()
+{
+    return (size_t)(2 * (BG * R + 2) * (BX + 4) + 3 * BG * R) * sizeof(float2) +
+           (size_t)BG * R * BX * sizeof(float);
+}
 
 template <typename S, int K, int BX, int BG, int R>
 static size_t smem_bytes()
@@ -377,7 +630,9 @@ static void cfg_info(int id, void **fn, size_t *smem)
     case 2: *fn = kernel_ptr<S, 4, 96, 8, 14>(); *smem = smem_bytes<S, 4, 96, 8, 14>(); break;
     case 3: *fn = kernel_ptr<S, 4, 96, 9, 12>(); *smem = smem_bytes<S, 4, 96, 9, 12>(); break;
     case 4: *fn = kernel_ptr<S, 2, 128, 8, 10>(); *smem = smem_bytes<S, 2, 128, 8, 10>(); break;
-    default: *fn = kernel_ptr<S, 6, 96, 4, 28>(); *smem = smem_bytes<S, 6, 96, 4, 28>(); break;
+    case 5: *fn = kernel_ptr<S, 6, 96, 4, 28>(); *smem = smem_bytes<S, 6, 96, 4, 28>(); break;
+    case 6: *fn = kernel_ptr_x2<S, 6, 96, 8, 14>(); *smem = smem_bytes_x2<S, 6, 96, 8, 14>(); break;
+    default: *fn = kernel_ptr_x2<S, 4, 96, 8, 14>(); *smem = smem_bytes_x2<S, 4, 96, 8, 14>(); break;
     }
 }
 
@@ -431,7 +686,7 @@ bool persist2d_plan(int id, int n0, int n1, int device, int *txo, int *tyo, int 
     }
     int per_sm = 0, nsm = 0;
     const PCfg c = kPCfgs[id];
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c.BX * c.BG, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, cfg_threads(c), smem) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -479,7 +734,8 @@ cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef
     cudaError_t e = cudaMemsetAsync(bar, 0, (4 + (size_t)ntx * nty * kPersistFlagStride) * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     count_launch();
-    return cudaLaunchCooperativeKernel(fn, dim3(ntx * nty), dim3(c.BX * c.BG), args, smem, st);
+    if (c.x2 && a.nfaces) return cudaErrorInvalidValue;     // the two-column kernel has no face terms
+    return cudaLaunchCooperativeKernel(fn, dim3(ntx * nty), dim3(cfg_threads(c)), args, smem, st);
 }
 
 // Self-test of the bounded grid barrier: the blocks wait for one more arrival
