@@ -145,7 +145,7 @@ bool launch_fused3d(int cfg, int lz, const Geom &g, const float2 *coef, const fl
 // Persistent exp action (2D, float storage types): see persist2d.cu.
 int persist2d_num_cfgs();
 int persist2d_cfg_k(int cfg);
-// whether configuration cfg adds ghost-point face terms (the two-column kernels do not)
+// whether configuration cfg adds ghost-point face terms
 bool persist2d_cfg_faces(int cfg);
 template <typename S>
 bool persist2d_plan(int cfg, int n0, int n1, int device, int *txo, int *tyo, int *ntx, int *nty);

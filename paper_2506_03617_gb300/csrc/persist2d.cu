@@ -355,8 +355,10 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
 // per point of k_persist2d.  Cells outside the grid start at zero, have y = 0
 // and meet only zero coefficients, so they stay exactly zero and every row pair
 // is stored unmasked; cells past the region's edge only spread garbage inward
-// by one cell per step, which the K-cell ring absorbs.  No ghost-point faces.
-template <typename S, int K, int BXH, int BG, int R, int CH>
+// by one cell per step, which the K-cell ring absorbs.  FACES = true adds the
+// ghost-point face terms as k_persist2d does (a separate instantiation, so the
+// face-free kernel keeps its register allocation).
+template <typename S, int K, int BXH, int BG, int R, int CH, bool FACES>
 __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, const S *__restrict__ x,
                                                              S *__restrict__ ex0,
                                                              S *__restrict__ ex1,
@@ -417,6 +419,7 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
 
     float2 y0r[R], y1r[R];
     unsigned inmask[2] = {0u, 0u}, tilemask[2] = {0u, 0u}, stripmask[2] = {0u, 0u};
+    unsigned facemask[2] = {0u, 0u};
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int ry = grp * R + r;
@@ -429,6 +432,10 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
             const int64_t q = in ? (int64_t)gy * n0 + gx[l] : 0;
             pv[l] = in ? St<S>::ld(x, q) : make_float2(0.f, 0.f);
             kap[l] = a.kappa[q];
+            if (FACES && in && a.nfaces &&
+                ((a.face[0] && gx[l] == 0) || (a.face[1] && gx[l] == n0 - 1) || (a.face[2] && gy == 0) ||
+                 (a.face[3] && gy == n1 - 1)))
+                facemask[l] |= 1u << r;
             if (in) {
                 inmask[l] |= 1u << r;
                 b0[(ry + 1) * PX + cx0 + l + 2] = pv[l];
@@ -516,6 +523,26 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
                 for (int j = 0; j < CH; ++j)
                     *reinterpret_cast<float4 *>(dst + (r0 + c + j + 1) * PX + cx0 + 2) = o[j];
             }
+            if (FACES && (facemask[0] | facemask[1])) {
+                // boundary rows of a ghost-point face: q gains face * p on those cells
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if ((facemask[l] >> r) & 1u) {
+                            const int ry = r0 + r, gy = gy0 + ry, gxl = gx[l];
+                            float2 f = make_float2(0.f, 0.f);
+                            if (a.face[0] && gxl == 0) f = cadd(f, a.face[0][gy]);
+                            if (a.face[1] && gxl == n0 - 1) f = cadd(f, a.face[1][gy]);
+                            if (a.face[2] && gy == 0) f = cadd(f, a.face[2][gxl]);
+                            if (a.face[3] && gy == n1 - 1) f = cadd(f, a.face[3][gxl]);
+                            const int ci = (ry + 1) * PX + cx0 + l + 2;
+                            const float2 fp = cmul(f, src[ci]);
+                            dst[ci] = make_float2(fmaf(-tau, fp.y, dst[ci].x), fmaf(tau, fp.x, dst[ci].y));
+                        }
+                    }
+                }
+            }
             __syncthreads();
         }
         if (a.w && ((pass + 1) % a.pass_per_sub) == 0) {
@@ -591,21 +618,23 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
 struct PCfg {
     int K, BX, BG, R;
     int x2;          // 1: two columns per thread (k_persist2d_x2, BX / 2 threads per row group)
+    int faces;       // adds ghost-point face terms
 };
-static const PCfg kPCfgs[] = {{2, 128, 4, 18, 0}, {4, 96, 4, 28, 0}, {4, 96, 8, 14, 0}, {4, 96, 9, 12, 0},
-                               {2, 128, 8, 10, 0}, {6, 96, 4, 28, 0}, {6, 96, 8, 14, 1}, {4, 96, 8, 14, 1}};
+static const PCfg kPCfgs[] = {{2, 128, 4, 18, 0, 1}, {4, 96, 4, 28, 0, 1}, {4, 96, 8, 14, 0, 1},
+                               {4, 96, 9, 12, 0, 1},  {2, 128, 8, 10, 0, 1}, {6, 96, 4, 28, 0, 1},
+                               {6, 96, 8, 14, 1, 0},  {4, 96, 8, 14, 1, 0},  {6, 96, 8, 14, 1, 1}};
 constexpr int kNumP = sizeof(kPCfgs) / sizeof(kPCfgs[0]);
 
 int persist2d_num_cfgs() { return kNumP; }
 int persist2d_cfg_k(int id) { return kPCfgs[id].K; }
-bool persist2d_cfg_faces(int id) { return id >= 0 && id < kNumP && !kPCfgs[id].x2; }
+bool persist2d_cfg_faces(int id) { return id >= 0 && id < kNumP && kPCfgs[id].faces; }
 static int cfg_threads(const PCfg &c) { return c.x2 ? c.BX / 2 * c.BG : c.BX * c.BG; }
 
 template <typename S, int K, int BX, int BG, int R>
 static void *kernel_ptr() { return (void *)k_persist2d<S, K, BX, BG, R, (R % 4 == 0) ? 4 : 2>; }
 
-template <typename S, int K, int BX, int BG, int R>
-static void *kernel_ptr_x2() { return (void *)k_persist2d_x2<S, K, BX / 2, BG, R, (R % 4 == 0) ? 4 : 2>; }
+template <typename S, int K, int BX, int BG, int R, bool F>
+static void *kernel_ptr_x2() { return (void *)k_persist2d_x2<S, K, BX / 2, BG, R, (R % 4 == 0) ? 4 : 2, F>; }
 
 template <typename S, int K, int BX, int BG, int R>
 static size_t smem_bytes_x2()
@@ -631,8 +660,9 @@ static void cfg_info(int id, void **fn, size_t *smem)
     case 3: *fn = kernel_ptr<S, 4, 96, 9, 12>(); *smem = smem_bytes<S, 4, 96, 9, 12>(); break;
     case 4: *fn = kernel_ptr<S, 2, 128, 8, 10>(); *smem = smem_bytes<S, 2, 128, 8, 10>(); break;
     case 5: *fn = kernel_ptr<S, 6, 96, 4, 28>(); *smem = smem_bytes<S, 6, 96, 4, 28>(); break;
-    case 6: *fn = kernel_ptr_x2<S, 6, 96, 8, 14>(); *smem = smem_bytes_x2<S, 6, 96, 8, 14>(); break;
-    default: *fn = kernel_ptr_x2<S, 4, 96, 8, 14>(); *smem = smem_bytes_x2<S, 4, 96, 8, 14>(); break;
+    case 6: *fn = kernel_ptr_x2<S, 6, 96, 8, 14, false>(); *smem = smem_bytes_x2<S, 6, 96, 8, 14>(); break;
+    case 7: *fn = kernel_ptr_x2<S, 4, 96, 8, 14, false>(); *smem = smem_bytes_x2<S, 4, 96, 8, 14>(); break;
+    default: *fn = kernel_ptr_x2<S, 6, 96, 8, 14, true>(); *smem = smem_bytes_x2<S, 6, 96, 8, 14>(); break;
     }
 }
 
@@ -734,7 +764,7 @@ cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef
     cudaError_t e = cudaMemsetAsync(bar, 0, (4 + (size_t)ntx * nty * kPersistFlagStride) * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     count_launch();
-    if (c.x2 && a.nfaces) return cudaErrorInvalidValue;     // the two-column kernel has no face terms
+    if (a.nfaces && !c.faces) return cudaErrorInvalidValue;   // this configuration has no face terms
     return cudaLaunchCooperativeKernel(fn, dim3(ntx * nty), dim3(cfg_threads(c)), args, smem, st);
 }
 

@@ -82,7 +82,7 @@ def test_low_precision_phi_with_faces(native, prec, bound):
         base[which] = got.cpu().numpy()
         assert _rel(base[which], ref) < bound
     ran = 0
-    for cfg in range(6):
+    for cfg in range(9):
         G.set_params(persist_cfg=cfg)
         if G.persist_config()[0] != cfg:
             continue

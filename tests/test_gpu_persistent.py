@@ -24,7 +24,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-N_PCFG = 8
+N_PCFG = 9
 
 
 @pytest.mark.parametrize("grid", [I.Grid(2, (290, 157), 6), I.Grid(2, (64, 64), 10),
