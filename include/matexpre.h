@@ -258,6 +258,15 @@ typedef enum {
  * May build the problem's TMA descriptors (no other side effect). */
 int mxp_sweep_kernel(mxp_problem *prob);
 
+/* Taylor plan of the exp / psi actions (host only, no device call): for a
+ * bound nu on ||t (A_s - mu)|| (shifted operator, Sec. 3.4) the number of
+ * sub-steps S >= nu / theta_max and the degree m per sub-step, a multiple of
+ * kmult, that minimise S m subject to the remainder bound
+ * S (nu/S)^(m+1) / (m+1)! e^(nu/S) <= tol.  Returns 1, or 0 for invalid
+ * arguments (outputs then unchanged).  No counterpart in the paper, which uses
+ * SLEPc's Krylov method for these actions. */
+int mxp_taylor_plan(double nu, double tol, double theta_max, int kmult, int *S, int *m);
+
 /* Tile planner of the persistent exp-action kernel (host only, no device
  * call; the paper has no counterpart).  Splits an n0 x n1 grid into at most
  * `slots` tiles of at most txmax x tymax cells, minimising the region (tile

@@ -1944,6 +1944,15 @@ mxp_status mxp_set_boundary(mxp_problem *P, const int *bc)
     return retune(P);
 }
 
+int mxp_taylor_plan(double nu, double tol, double theta_max, int kmult, int *S, int *m)
+{
+    if (!S || !m || !(nu >= 0) || !(tol > 0 && tol < 1) || !(theta_max > 0) || kmult < 1) return 0;
+    const TaylorPlan pl = make_plan(nu, tol, theta_max, kmult);
+    *S = pl.S;
+    *m = pl.m;
+    return 1;
+}
+
 int mxp_sweep_kernel(mxp_problem *P)
 {
     if (!P) return -1;

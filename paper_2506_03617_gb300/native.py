@@ -111,6 +111,8 @@ SIGNATURES = {
     "mxp_set_boundary": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_get_boundary": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_sweep_kernel": (ct.c_int, [ct.c_void_p]),
+    "mxp_taylor_plan": (ct.c_int, [ct.c_double, ct.c_double, ct.c_double, ct.c_int,
+                                   ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "mxp_persist_tile_plan": (ct.c_int, [ct.c_int] * 6 + [ct.POINTER(ct.c_int)] * 4),
     "mxp_destroy": (None, [ct.c_void_p]),
     "mxp_status_string": (ct.c_char_p, [ct.c_int]),
@@ -374,6 +376,13 @@ class Cnn:
 def attach_cnn(problem, net, accept_tol=0.5):
     _check(load().mxp_attach_cnn(problem._h, net._h if net is not None else None,
                                  float(accept_tol)))
+
+
+def taylor_plan(nu, tol, theta_max, kmult=1):
+    """(sub-steps S, degree m) of the library's Taylor plan, or None."""
+    S, m = ct.c_int(0), ct.c_int(0)
+    ok = load().mxp_taylor_plan(float(nu), float(tol), float(theta_max), int(kmult), ct.byref(S), ct.byref(m))
+    return (int(S.value), int(m.value)) if ok else None
 
 
 def persist_tile_plan(n0, n1, slots, k, txmax, tymax):
