@@ -255,7 +255,8 @@ typedef enum {
     MXP_SWEEP_ZMARCH_TMA_3D = 5   /* one launch per step, planes staged by TMA (n0 % 4 == 0) */
 } mxp_sweep_kind;
 /* Returns an mxp_sweep_kind, or -1 for a NULL problem or a failed set-up.
- * May build the problem's TMA descriptors (no other side effect). */
+ * For 3D low-precision problems it may allocate the problem's work buffers and
+ * build their TMA descriptors (as the first action would). */
 int mxp_sweep_kernel(mxp_problem *prob);
 
 /* Taylor plan of the exp / psi actions (host only, no device call): for a
