@@ -241,9 +241,10 @@ def recorded_traffic(kernel, prec):
 KERNEL_NAMES = {"horner_step": "k_step", "fused2d": "k_fused2d", "persist2d": "k_persist2d"}
 
 
-def record_traffic(kernel, prec, csv_path):
+def record_traffic(kernel, prec, csv_path, out_path=None):
     """DRAM bytes per launch of `kernel` from an ncu CSV log (one row per
-    launch and metric), stored with the hash of the kernel's source file."""
+    launch and metric), stored with the hash of the kernel's source file in
+    out_path (default profiles/traffic.json)."""
     import csv
     per_launch = {}
     with open(csv_path, newline="") as fh:
@@ -262,7 +263,7 @@ def record_traffic(kernel, prec, csv_path):
             per_launch[r[iid]] = per_launch.get(r[iid], 0.0) + float(r[ival].replace(",", ""))
     if not per_launch:
         raise SystemExit(f"no {KERNEL_NAMES[kernel]} launches with DRAM metrics in {csv_path}")
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = out_path or os.path.join(ROOT, "profiles", "traffic.json")
     rec = {}
     if os.path.exists(path):
         with open(path) as fh:
