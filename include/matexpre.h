@@ -180,9 +180,12 @@ typedef enum {
  * points; normally with npml = 0).  The face lies midway between a boundary
  * unknown and its ghost; the ghost's coefficient joins the diagonal of the
  * boundary rows of A and A_s.  With any non-Dirichlet face the exp / psi
- * actions use the per-pass unfused sweep (the tiled and persistent kernels
- * assume zero ghosts).  Copies bc; allocates the face terms on the problem's
- * device (MXP_ENOMEM on failure); MXP_EINVAL for an unknown code. */
+ * actions run on kernels that carry these face terms: in 2D (complex64 and
+ * bfloat16 storage) the persistent exp-action kernel when one of its face
+ * configurations fits the grid, otherwise the per-point sweep; the tiled
+ * per-pass kernels (fused 2D, z-marching 3D) assume zero ghosts and are not
+ * used.  Copies bc; allocates the face terms on the problem's device
+ * (MXP_ENOMEM on failure); MXP_EINVAL for an unknown code. */
 mxp_status mxp_set_boundary(mxp_problem *prob, const int *bc);
 mxp_status mxp_get_boundary(const mxp_problem *prob, int *bc);
 
@@ -245,6 +248,10 @@ int mxp_num_tile_configs(void);
 int mxp_tile_config(const mxp_problem *prob, int *fuse_k);
 /* Persistent exp-action kernel in use (-1 = none) and its tile count. */
 int mxp_persist_config(const mxp_problem *prob, int *ntiles);
+/* Its tiles: extents txo x tyo, counts ntx x nty (one CTA each) and the steps
+ * K per exchange (each CTA updates its tile plus a K-cell ring); returns the
+ * configuration (-1 = none, extents then 0) or -1 for a NULL argument. */
+int mxp_persist_geometry(const mxp_problem *prob, int *txo, int *tyo, int *ntx, int *nty, int *k);
 
 /* Kernel that runs the exp-action sweeps of the problem (the choice of the
  * autotuner and of the grid; no counterpart in the paper). */
@@ -282,18 +289,20 @@ int mxp_persist_tile_plan(int n0, int n1, int slots, int k, int txmax, int tymax
 
 /* Allocation-free exp / psi_1 action.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory when they need an
- * action -- code running while a CUDA graph is being captured, plugins whose
- * host application owns all device memory through its own pool, or loops that
- * cannot afford a cudaMalloc (which may synchronise the device).
+ * action -- plugins whose host application owns all device memory through its
+ * own pool, or loops that cannot afford a cudaMalloc (which may synchronise the
+ * device).
  *
  * Computes y = exp(i t A_s) x (which = 0) or y = psi_1(i t A_s) x (which = 1)
- * in complex128 exactly like mxp_apply_phi with prec = MXP_C128, without a
- * problem handle: grid and params (omega, c_pml, shift_s, t, exp_tol,
- * theta_max; the other fields are ignored) describe the problem, c_dev is the
- * wave speed on the device (prod_d n_d doubles, x fastest, finite and > 0),
- * x_dev / y_dev are caller-owned complex128 device vectors (not aliased), work
- * is ordered on cuda_stream (NULL = legacy default stream), and the stream is
- * synchronised once during the call (to read the range of c).
+ * in complex128 with the shift and Taylor plan of mxp_apply_phi (prec =
+ * MXP_C128; the same host planning code), without a problem handle: grid and
+ * params (omega, c_pml, shift_s, t, exp_tol, theta_max; the other fields are
+ * ignored) describe the problem, c_dev is the wave speed on the device
+ * (prod_d n_d doubles, x fastest, finite and > 0, else MXP_EINVAL), x_dev /
+ * y_dev are caller-owned complex128 device vectors (not aliased), work is
+ * ordered on cuda_stream (NULL = legacy default stream).  Every call copies the
+ * range of c to the host and synchronises the stream once, since the shift and
+ * the plan are chosen on the host from it.
  *
  * All workspace lives in one fixed device array compiled into the library:
  * at most 262,144 unknowns, 4,096 unknowns per axis and 64 PML cells per side
@@ -302,7 +311,7 @@ int mxp_persist_tile_plan(int n0, int n1, int slots, int k, int txmax, int tymax
  * The call makes no device allocation.  Calls share the array: calls whose
  * work overlaps on the GPU (other streams, other host threads) race and must be
  * ordered by the caller.  The first call on a device looks up the array's
- * address and should come before any stream capture begins. */
+ * device address. */
 mxp_status mxp_apply_phi_noalloc(const mxp_grid *grid, const mxp_params *params,
                                  const double *c_dev, int which, const void *x_dev,
                                  void *y_dev, void *cuda_stream, int64_t *passes_out);
@@ -343,10 +352,22 @@ mxp_status mxp_attach_cnn(mxp_problem *prob, mxp_cnn *net, double accept_tol);
 
 /* Failure-detection self-test (no counterpart in the paper): launches the
  * bounded device-side wait used by the persistent kernel's grid barrier with an
- * arrival that never happens; the wait gives up after a few thousand polls,
- * sets the problem's error word and the call returns MXP_ETIMEOUT.  The
- * problem stays usable afterwards. */
+ * arrival that never happens; the wait gives up after a few thousand polls and
+ * sets the problem's error word.  When the problem uses the persistent
+ * exp-action kernel, one such action (on the problem's work buffers) follows
+ * before the host reads the word, which shows that a later launch keeps the
+ * error of an earlier one.  The call returns MXP_ETIMEOUT and the problem stays
+ * usable afterwards. */
 mxp_status mxp_selftest_barrier_timeout(mxp_problem *prob);
+
+/* Measured FMA throughput of `device` in flop/s (2 flops per fused
+ * multiply-add): *fp32_flops for float, *fp64_flops for double.  Independent
+ * FMA chains on every SM, timed with CUDA events (best of three after a
+ * warm-up launch); no clock or power setting is touched.  These are the
+ * arithmetic ceilings of the rooflines of the sweep kernels that run from
+ * on-chip memory and of the complex128 path.  Allocates and frees a small
+ * device buffer; synchronises the device.  No counterpart in the paper. */
+mxp_status mxp_measure_fma_peak(int device, double *fp32_flops, double *fp64_flops);
 
 /* Number of unknowns prod_d n_d of the problem. */
 int64_t mxp_num_unknowns(const mxp_problem *prob);

@@ -312,7 +312,7 @@ __global__ void k_unpack_output(const float *__restrict__ y, int64_t n, double2 
 static int ew_grid(int64_t n)
 {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > (int64_t)sm_count() * 8) b = (int64_t)sm_count() * 8;
     return (int)std::max<int64_t>(b, 1);
 }
 

@@ -55,12 +55,6 @@ static mxp_status fail(mxp_status s, const std::string &msg)
         if (s_ != MXP_OK) return s_;             \
     } while (0)
 
-struct TaylorPlan {
-    int S = 1;      // sub-steps
-    int m = 1;      // Taylor degree per sub-step
-    double nu = 0;  // norm bound used
-};
-
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int d)
@@ -205,84 +199,6 @@ static std::vector<int> axis_classes(const mxp_problem *P, int d)
     return out;
 }
 
-// nu(mu) = t * max over (axis classes, kappa in {kmin, kmax}) of
-//          sum_d (|wp_d| + |wm_d|) + |kappa (1 + i s) - sum_d wc_d - mu|.
-// This bounds ||t (A_s - mu I)||_inf from above (the medium may vary inside a
-// class; |.| is convex in kappa so its endpoints bound it).
-struct NormTable {
-    std::vector<double> off;    // per combination
-    std::vector<cd> wcs;        // per combination
-};
-
-static NormTable norm_table(const mxp_problem *P)
-{
-    NormTable T;
-    const int nm = P->geom.nmax;
-    std::vector<int> cls[3];
-    for (int d = 0; d < 3; ++d) cls[d] = (d < P->grid.dim) ? axis_classes(P, d) : std::vector<int>{-1};
-    for (int i0 : cls[0])
-        for (int i1 : cls[1])
-            for (int i2 : cls[2]) {
-                int idx[3] = {i0, i1, i2};
-                double off = 0;
-                cd wcs = 0;
-                for (int d = 0; d < P->grid.dim; ++d) {
-                    const double2 wp = P->coef_host[(size_t)(3 * d) * nm + idx[d]];
-                    const double2 wm = P->coef_host[(size_t)(3 * d + 1) * nm + idx[d]];
-                    const double2 wc = P->coef_host[(size_t)(3 * d + 2) * nm + idx[d]];
-                    off += std::hypot(wp.x, wp.y) + std::hypot(wm.x, wm.y);
-                    wcs += cd(wc.x, wc.y);
-                }
-                T.off.push_back(off);
-                T.wcs.push_back(wcs);
-            }
-    return T;
-}
-
-static double nu_of_mu(const mxp_problem *P, const NormTable &T, double mu)
-{
-    const double w2 = P->prm.omega * P->prm.omega;
-    const double kap[2] = {w2 / (P->cmax * P->cmax), w2 / (P->cmin * P->cmin)};
-    const cd z(1.0, P->prm.shift_s);
-    double best = 0;
-    for (size_t c = 0; c < T.off.size(); ++c)
-        for (double k : kap) {
-            const double v = T.off[c] + std::abs(k * z - T.wcs[c] - mu);
-            if (v > best) best = v;
-        }
-    return P->prm.t * best;
-}
-
-static TaylorPlan make_plan(double nu, double tol, double theta_max, int kmult)
-{
-    TaylorPlan best;
-    best.nu = nu;
-    if (!(nu > 0)) {
-        best.S = 1;
-        best.m = kmult;
-        return best;
-    }
-    const int Smin = std::max(1, (int)std::ceil(nu / theta_max));
-    long best_cost = -1;
-    for (int S = Smin; S <= 4 * Smin + 8; ++S) {
-        const double th = nu / S;
-        const double lt = std::log(tol);
-        int m = 1;
-        for (; m < 400; ++m) {
-            const double lg = std::log((double)S) + (m + 1) * std::log(th) - std::lgamma(m + 2.0) + th;
-            if (lg <= lt) break;
-        }
-        if (kmult > 1) m = ((m + kmult - 1) / kmult) * kmult;
-        const long cost = (long)m * S;
-        if (best_cost < 0 || cost < best_cost) {
-            best_cost = cost;
-            best.S = S;
-            best.m = m;
-        }
-    }
-    return best;
-}
-
 static int effective_fuse(const mxp_problem *P)
 {
     return P->fused_cfg >= 0 ? fused2d_cfg_k(P->fused_cfg) : 1;
@@ -359,26 +275,22 @@ static mxp_status upload_tau(mxp_problem *P)
 
 static void update_plans(mxp_problem *P)
 {
-    const NormTable T = norm_table(P);
-    // golden-section search for the mu minimising the convex nu(mu)
+    // per-axis coefficient classes (every PML index plus one interior index)
+    AxisClasses cls[3];
+    const int nm = P->geom.nmax;
+    for (int d = 0; d < P->grid.dim; ++d)
+        for (int i : axis_classes(P, d)) {
+            const double2 wp = P->coef_host[(size_t)(3 * d) * nm + i];
+            const double2 wm = P->coef_host[(size_t)(3 * d + 1) * nm + i];
+            const double2 wc = P->coef_host[(size_t)(3 * d + 2) * nm + i];
+            cls[d].off.push_back(std::hypot(wp.x, wp.y) + std::hypot(wm.x, wm.y));
+            cls[d].wc.push_back(cd(wc.x, wc.y));
+        }
     const double w2 = P->prm.omega * P->prm.omega;
-    double lo = -1e300, hi = 1e300;
-    for (size_t c = 0; c < T.wcs.size(); ++c) {
-        const double k1 = w2 / (P->cmax * P->cmax), k2 = w2 / (P->cmin * P->cmin);
-        const double r1 = k1 - T.wcs[c].real(), r2 = k2 - T.wcs[c].real();
-        lo = (lo == -1e300) ? std::min(r1, r2) : std::min(lo, std::min(r1, r2));
-        hi = (hi == 1e300) ? std::max(r1, r2) : std::max(hi, std::max(r1, r2));
-    }
-    const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
-    double a = lo, b = hi;
-    double x1 = b - gr * (b - a), x2 = a + gr * (b - a);
-    double f1 = nu_of_mu(P, T, x1), f2 = nu_of_mu(P, T, x2);
-    for (int it = 0; it < 200 && (b - a) > 1e-12 * (std::abs(a) + std::abs(b) + 1); ++it) {
-        if (f1 < f2) { b = x2; x2 = x1; f2 = f1; x1 = b - gr * (b - a); f1 = nu_of_mu(P, T, x1); }
-        else { a = x1; x1 = x2; f1 = f2; x2 = a + gr * (b - a); f2 = nu_of_mu(P, T, x2); }
-    }
-    P->mu = 0.5 * (a + b);
-    P->nu = nu_of_mu(P, T, P->mu);
+    const ShiftChoice sh = choose_shift(cls, P->grid.dim, w2 / (P->cmax * P->cmax), w2 / (P->cmin * P->cmin),
+                                        P->prm.shift_s, P->prm.t);
+    P->mu = sh.mu;
+    P->nu = sh.nu;
     P->nu_aug = std::max(P->nu, std::abs(P->prm.t * P->mu));
     P->nu_aug2 = std::max(P->nu, std::abs(P->prm.t * P->mu) + 1.0);   // Jordan block of psi_2
     make_plans(P);
@@ -478,7 +390,7 @@ static mxp_status ensure_base(mxp_problem *P)
     if (!P->tmp) CK(cudaMalloc(&P->tmp, n * sizeof(double2)));
     if (!P->tmp2) CK(cudaMalloc(&P->tmp2, n * sizeof(double2)));
     if (!P->ks.partials) {
-        P->ks.grid = 152 * 4;
+        P->ks.grid = sm_count() * 4;
         CK(cudaMalloc(&P->ks.partials, (size_t)P->ks.grid * kChunk * sizeof(double2)));
     }
     if (!P->host_scal) CK(cudaMallocHost(&P->host_scal, 8 * sizeof(double)));
@@ -581,8 +493,7 @@ static mxp_status tune_fused(mxp_problem *P)
     S *b0 = (S *)P->hb[0], *b1 = (S *)P->hb[1], *b2 = (S *)P->hb[2];
     CK(cudaMemsetAsync(b0, 0, (size_t)n * sizeof(S), P->stream));
     CK(cudaMemsetAsync(b1, 0, (size_t)n * sizeof(S), P->stream));
-    int nsm = 152;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
+    const int nsm = sm_count();
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1944,15 +1855,6 @@ mxp_status mxp_set_boundary(mxp_problem *P, const int *bc)
     return retune(P);
 }
 
-int mxp_taylor_plan(double nu, double tol, double theta_max, int kmult, int *S, int *m)
-{
-    if (!S || !m || !(nu >= 0) || !(tol > 0 && tol < 1) || !(theta_max > 0) || kmult < 1) return 0;
-    const TaylorPlan pl = make_plan(nu, tol, theta_max, kmult);
-    *S = pl.S;
-    *m = pl.m;
-    return 1;
-}
-
 int mxp_sweep_kernel(mxp_problem *P)
 {
     if (!P) return -1;
@@ -2009,6 +1911,15 @@ mxp_status mxp_selftest_barrier_timeout(mxp_problem *P)
     DeviceGuard guard(P->device);
     CKS(ensure_base(P));
     CK(barrier_selftest(P->bar, P->stream));
+    // a persistent launch between the timed-out wait and the host's read must not
+    // erase the error word (it finds the word set and leaves its pass loop)
+    if (P->persist_cfg >= 0) {
+        const cudaError_t ce = (P->prm.prec == MXP_BF16S)
+                                   ? persist_action<__nv_bfloat162>(P, (const __nv_bfloat162 *)P->hb[0],
+                                                                    (__nv_bfloat162 *)P->hb[1])
+                                   : persist_action<float2>(P, (const float2 *)P->hb[0], (float2 *)P->hb[1]);
+        CK(ce);
+    }
     return read_scal(P, nullptr, 0);   // MXP_ETIMEOUT when the wait ran out (and clears it)
 }
 
@@ -2026,6 +1937,17 @@ int mxp_persist_config(const mxp_problem *P, int *ntiles)
 {
     if (!P) return -1;
     if (ntiles) *ntiles = P->persist_cfg >= 0 ? P->p_ntx * P->p_nty : 0;
+    return P->persist_cfg;
+}
+
+int mxp_persist_geometry(const mxp_problem *P, int *txo, int *tyo, int *ntx, int *nty, int *k)
+{
+    if (!P || !txo || !tyo || !ntx || !nty || !k) return -1;
+    *txo = P->p_txo;
+    *tyo = P->p_tyo;
+    *ntx = P->p_ntx;
+    *nty = P->p_nty;
+    *k = P->persist_cfg >= 0 ? persist2d_cfg_k(P->persist_cfg) : 0;
     return P->persist_cfg;
 }
 

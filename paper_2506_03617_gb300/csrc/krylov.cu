@@ -113,7 +113,7 @@ __global__ void k_maxpy(double2 *__restrict__ w, const double2 *__restrict__ V, 
 static int grid_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > (int64_t)sm_count() * 8) b = (int64_t)sm_count() * 8;
     if (b < 1) b = 1;
     return (int)b;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <atomic>
+#include <complex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -18,6 +19,34 @@ void note_error(const char *msg);
 // Number of kernels this library has launched (process-wide).
 extern std::atomic<long long> g_launch_count;
 inline void count_launch(int n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
+
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count();
+
+// ---------------------------------------------------------------- planning (plan.cu, host)
+// Taylor plan of one exp / psi action: S sub-steps of a degree-m polynomial.
+struct TaylorPlan {
+    int S = 1;      // sub-steps
+    int m = 1;      // Taylor degree per sub-step
+    double nu = 0;  // norm bound used
+};
+// (S, m) minimising S*m with S (nu/S)^(m+1)/(m+1)! e^(nu/S) <= tol and
+// nu/S <= theta_max; m rounded up to a multiple of kmult.
+TaylorPlan make_plan(double nu, double tol, double theta_max, int kmult);
+// Distinct coefficient classes of one axis: |wp| + |wm| and wc = wp + wm of
+// every PML position plus one interior position.
+struct AxisClasses {
+    std::vector<double> off;
+    std::vector<std::complex<double>> wc;
+};
+struct ShiftChoice {
+    double mu = 0;   // real shift
+    double nu = 0;   // row-sum bound of t (A_s - mu I) at that shift
+};
+// The shift mu minimising the row-sum bound of t (A_s - mu I) over the axis
+// classes and omega^2/c^2 in [kmin, kmax] (golden-section search).
+ShiftChoice choose_shift(const AxisClasses *cls, int dim, double kmin, double kmax, double shift_s,
+                         double t);
 
 // ---------------------------------------------------------------- complex math
 __host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }

@@ -1,22 +1,22 @@
 // Allocation-free exp / psi_1 action (mxp_apply_phi_noalloc).
 //
 // Some callers cannot allocate device memory at the point where they need an
-// action: code that runs while a CUDA graph is being captured, plugins whose
-// host framework owns every byte of device memory through its own pool, and
-// latency-critical loops where a cudaMalloc (which may synchronise the device)
-// is not acceptable.  This entry point serves them: it takes plain device
-// pointers for the medium, the input and the output, and keeps all of its
-// workspace (the per-axis coefficient table, omega^2/c^2 and the three Taylor
-// buffers) in one fixed array that is part of the library image.
+// action: plugins whose host application owns every byte of device memory
+// through its own pool, and loops where a cudaMalloc (which may synchronise the
+// device) is not acceptable.  This entry point serves them: it takes plain
+// device pointers for the medium, the input and the output, and keeps all of
+// its workspace (the per-axis coefficient table, omega^2/c^2 and the three
+// Taylor buffers) in one fixed array that is part of the library image.
 //
 // The array below holds kNoAllocMaxUnknowns unknowns worth of workspace
 // (about 16 MB); every GPU that loads the library reserves it until the
 // process exits.  Calls share it: two calls whose work overlaps on the GPU
 // (different streams, or host threads racing) corrupt each other, so callers
 // must order them.  The first call on a device looks up the array's device
-// address (cudaGetSymbolAddress) and should therefore happen before any
-// stream capture starts; later calls only launch kernels and copy between
-// device buffers.
+// address (cudaGetSymbolAddress).  Every call reads the range of c back to the
+// host and synchronises its stream once, because the shift and the Taylor plan
+// are chosen on the host from that range (by the same planning code as the
+// problem path, plan.cu).
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -37,7 +37,7 @@ constexpr size_t kCoefOff = 0;
 constexpr size_t kKappaOff = kCoefOff + (size_t)9 * kNoAllocMaxAxis * 2;
 constexpr size_t kBufOff = kKappaOff + (size_t)kNoAllocMaxUnknowns;
 constexpr size_t kMinMaxOff = kBufOff + (size_t)3 * 2 * kNoAllocMaxUnknowns;
-constexpr size_t kScratchDoubles = kMinMaxOff + 8;
+constexpr size_t kScratchDoubles = kMinMaxOff + 8;   // min, max, non-finite / non-positive flag
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -100,12 +100,15 @@ __global__ void k_noalloc_kappa(const double *__restrict__ c, double w2, int64_t
     double *kap = g_noalloc_scratch + kKappaOff;
     __shared__ double smin[256], smax[256];
     double lo = 1e300, hi = 0.0;
+    int bad = 0;
     for (int64_t p = threadIdx.x; p < n; p += blockDim.x) {
         const double v = c[p];
         kap[p] = w2 / (v * v);
         lo = fmin(lo, v);
         hi = fmax(hi, v);
+        bad |= !(v > 0.0) || !isfinite(v);   // fmin / fmax skip NaN: flag it here
     }
+    bad = __syncthreads_or(bad);
     smin[threadIdx.x] = lo;
     smax[threadIdx.x] = hi;
     __syncthreads();
@@ -119,6 +122,7 @@ __global__ void k_noalloc_kappa(const double *__restrict__ c, double w2, int64_t
     if (threadIdx.x == 0) {
         g_noalloc_scratch[kMinMaxOff] = smin[0];
         g_noalloc_scratch[kMinMaxOff + 1] = smax[0];
+        g_noalloc_scratch[kMinMaxOff + 2] = bad ? 1.0 : 0.0;
     }
 }
 
@@ -184,25 +188,18 @@ extern "C" mxp_status mxp_apply_phi_noalloc(const mxp_grid *grid, const mxp_para
     // per-axis PML coefficients, omega^2/c^2 and the range of c, on the device
     k_noalloc_coef<<<8, 256, 0, st>>>(ag, grid->dim, grid->npml, grid->h, prm->c_pml, prm->omega, nmax);
     k_noalloc_kappa<<<1, 256, 0, st>>>(c_dev, prm->omega * prm->omega, ntot);
-    double mm[2] = {0, 0};
-    if (cudaMemcpyAsync(mm, scr + kMinMaxOff, 2 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    double mm[3] = {0, 0, 0};
+    if (cudaMemcpyAsync(mm, scr + kMinMaxOff, 3 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return nfail(MXP_ECUDA, "setting up the allocation-free action failed");
-    if (!(mm[0] > 0) || !std::isfinite(mm[1])) return nfail(MXP_EINVAL, "wave speed must be finite and > 0");
+    if (mm[2] != 0.0 || !(mm[0] > 0) || !std::isfinite(mm[1]))
+        return nfail(MXP_EINVAL, "wave speed must be finite and > 0");
 
-    // Shift mu minimising the row-sum bound nu(mu) = t max (off + |kappa (1+is) - wc - mu|)
-    // over the distinct PML positions of each axis and kappa in {min, max}
-    // (fixed-size tables on the stack: at most 2 * 64 + 1 positions per axis).
-    constexpr int kCls = 2 * kNoAllocMaxPml + 1;
-    double off_t[3][kCls];
-    cd wc_t[3][kCls];
-    int ncls[3] = {1, 1, 1};
+    // shift mu and Taylor plan from the same host planning code as the problem
+    // path: coefficient classes of every PML position plus one interior position
+    AxisClasses cls[3];
     const double ih2 = 1.0 / (grid->h * grid->h);
-    for (int d = 0; d < 3; ++d) {
-        off_t[d][0] = 0;
-        wc_t[d][0] = 0;
-        if (d >= grid->dim) continue;
-        int k = 0;
+    for (int d = 0; d < grid->dim; ++d) {
         const int n = ag.n[d], p = grid->npml;
         for (int i = 0; i < n; ++i) {
             if (!(i < p || i >= n - p || i == p)) continue;
@@ -212,60 +209,19 @@ extern "C" mxp_status mxp_apply_phi_noalloc(const mxp_grid *grid, const mxp_para
             inv_stretch_nd(x + 0.5 * grid->h, ag.L[d], p, grid->h, prm->c_pml, prm->omega, &pr, &pi);
             inv_stretch_nd(x - 0.5 * grid->h, ag.L[d], p, grid->h, prm->c_pml, prm->omega, &mr, &mi);
             const cd wp = cd(ar, ai) * cd(pr, pi) * ih2, wm = cd(ar, ai) * cd(mr, mi) * ih2;
-            off_t[d][k] = std::abs(wp) + std::abs(wm);
-            wc_t[d][k] = wp + wm;
-            ++k;
+            cls[d].off.push_back(std::abs(wp) + std::abs(wm));
+            cls[d].wc.push_back(wp + wm);
         }
-        ncls[d] = k;
     }
     const double w2 = prm->omega * prm->omega;
-    const double kap[2] = {w2 / (mm[1] * mm[1]), w2 / (mm[0] * mm[0])};
-    const cd z(1.0, prm->shift_s);
-    auto nu_of = [&](double mu) {
-        double best = 0;
-        for (int a = 0; a < ncls[0]; ++a)
-            for (int b = 0; b < ncls[1]; ++b)
-                for (int c = 0; c < ncls[2]; ++c) {
-                    const double off = off_t[0][a] + off_t[1][b] + off_t[2][c];
-                    const cd wcs = wc_t[0][a] + wc_t[1][b] + wc_t[2][c];
-                    for (double kk : kap) best = std::max(best, off + std::abs(kk * z - wcs - mu));
-                }
-        return prm->t * best;
-    };
-    double lo = 1e300, hi = -1e300;
-    for (int a = 0; a < ncls[0]; ++a)
-        for (int b = 0; b < ncls[1]; ++b)
-            for (int c = 0; c < ncls[2]; ++c)
-                for (double kk : kap) {
-                    const double r = kk - (wc_t[0][a] + wc_t[1][b] + wc_t[2][c]).real();
-                    lo = std::min(lo, r);
-                    hi = std::max(hi, r);
-                }
-    const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
-    double x1 = hi - gr * (hi - lo), x2 = lo + gr * (hi - lo);
-    double f1 = nu_of(x1), f2 = nu_of(x2);
-    for (int it = 0; it < 80 && (hi - lo) > 1e-12 * (std::abs(lo) + std::abs(hi) + 1); ++it) {
-        if (f1 < f2) { hi = x2; x2 = x1; f2 = f1; x1 = hi - gr * (hi - lo); f1 = nu_of(x1); }
-        else { lo = x1; x1 = x2; f1 = f2; x2 = lo + gr * (hi - lo); f2 = nu_of(x2); }
-    }
-    const double mu = 0.5 * (lo + hi);
-    const double nu = nu_of(mu);
-    const double nu_plan = which ? std::max(nu, std::abs(prm->t * mu)) : nu;
+    const ShiftChoice sh = choose_shift(cls, grid->dim, w2 / (mm[1] * mm[1]), w2 / (mm[0] * mm[0]),
+                                        prm->shift_s, prm->t);
+    const double mu = sh.mu;
+    const double nu_plan = which ? std::max(sh.nu, std::abs(prm->t * mu)) : sh.nu;
     const double tol = which ? prm->exp_tol * 0.1 : prm->exp_tol;
     const double theta = prm->theta_max > 0 ? prm->theta_max : 6.0;
-    // (sub-steps S, degree m) minimising S*m with S (nu/S)^(m+1)/(m+1)! e^(nu/S) <= tol
-    int Sbest = 1, mbest = 1;
-    if (nu_plan > 0) {
-        const int Smin = std::max(1, (int)std::ceil(nu_plan / theta));
-        long cost_best = -1;
-        for (int S = Smin; S <= 4 * Smin + 8; ++S) {
-            const double th = nu_plan / S;
-            int m = 1;
-            for (; m < 400; ++m)
-                if (std::log((double)S) + (m + 1) * std::log(th) - std::lgamma(m + 2.0) + th <= std::log(tol)) break;
-            if (cost_best < 0 || (long)m * S < cost_best) { cost_best = (long)m * S; Sbest = S; mbest = m; }
-        }
-    }
+    const TaylorPlan plan = make_plan(nu_plan, tol, theta, 1);
+    const int Sbest = plan.S, mbest = plan.m;
 
     // Taylor-Horner sweeps on the shifted (augmented) matrix, as in the problem path
     Geom g{};

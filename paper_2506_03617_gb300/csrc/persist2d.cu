@@ -761,7 +761,12 @@ cudaError_t launch_persist2d(int id, const Geom &g, int npml, const float2 *coef
     }
     void *args[] = {&a, (void *)&x, (void *)&ex0, (void *)&ex1, (void *)&out};
     const PCfg c = kPCfgs[id];
-    cudaError_t e = cudaMemsetAsync(bar, 0, (4 + (size_t)ntx * nty * kPersistFlagStride) * sizeof(unsigned), st);
+    // reset the arrival count, the generation and the tile epochs, but not the
+    // error word bar[2]: a timeout of an earlier launch stays set until the host
+    // reads it (and a launch that finds it set leaves its pass loop at once)
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(bar + 4, 0, (size_t)ntx * nty * kPersistFlagStride * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     count_launch();
     if (a.nfaces && !c.faces) return cudaErrorInvalidValue;   // this configuration has no face terms
@@ -778,7 +783,7 @@ __global__ void k_barrier_selftest(unsigned *bar, unsigned expected, long long l
 
 cudaError_t barrier_selftest(unsigned *bar, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     count_launch();
     k_barrier_selftest<<<2, 32, 0, st>>>(bar, 3u, 20000);

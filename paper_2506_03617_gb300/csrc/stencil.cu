@@ -13,6 +13,22 @@
 
 namespace mxp {
 
+int sm_count()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            return 152;
+        }
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 template <typename C>
 __device__ __forceinline__ C czero() { return CT<C>::mk(0, 0); }
 
@@ -153,11 +169,11 @@ __global__ void __launch_bounds__(256) k_step3z(Geom g, const typename St<S>::C 
 }
 
 // Planes per z segment: enough segments for about four waves of 256-thread
-// blocks at eight blocks per SM on 152 SMs, at least four planes each.
+// blocks at eight blocks per SM, at least four planes each.
 static int z_segment(const Geom &g)
 {
     const int64_t bxy = (int64_t)((g.n[0] + 31) / 32) * ((g.n[1] + 7) / 8);
-    const int64_t want = 152 * 8 * 4;
+    const int64_t want = (int64_t)sm_count() * 8 * 4;
     int64_t nseg = (want + bxy - 1) / bxy;
     if (nseg < 1) nseg = 1;
     int lz = (int)((g.n[2] + nseg - 1) / nseg);
@@ -235,7 +251,7 @@ __global__ void k_convert_out(const S *__restrict__ x, double2 *__restrict__ out
 static int stream_grid(int64_t n)
 {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > (int64_t)sm_count() * 16) b = (int64_t)sm_count() * 16;
     if (b < 1) b = 1;
     return (int)b;
 }

@@ -351,7 +351,7 @@ static cudaError_t launch3t(const Geom &g, const typename St<S>::C *coef, const 
     }
     // segment length: about four waves of blocks
     const int64_t bxy = (int64_t)((g.n[0] + kTX - 1) / kTX) * ((g.n[1] + kTY - 1) / kTY);
-    int64_t nseg = (152 * 4 * 4 + bxy - 1) / bxy;
+    int64_t nseg = ((int64_t)sm_count() * 4 * 4 + bxy - 1) / bxy;
     if (nseg < 1) nseg = 1;
     int lz = (int)((g.n[2] + nseg - 1) / nseg);
     if (lz < 8) lz = 8;

@@ -91,6 +91,7 @@ SIGNATURES = {
                                          ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
                                          ct.c_void_p, ct.POINTER(ct.c_int64)]),
     "mxp_num_unknowns": (ct.c_int64, [ct.c_void_p]),
+    "mxp_measure_fma_peak": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
     "mxp_cnn_num_params": (ct.c_int64, []),
     "mxp_cnn_create": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int,
                                   ct.POINTER(ct.c_void_p)]),
@@ -108,6 +109,7 @@ SIGNATURES = {
     "mxp_num_tile_configs": (ct.c_int, []),
     "mxp_tile_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_persist_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
+    "mxp_persist_geometry": (ct.c_int, [ct.c_void_p] + [ct.POINTER(ct.c_int)] * 5),
     "mxp_set_boundary": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_get_boundary": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_sweep_kernel": (ct.c_int, [ct.c_void_p]),
@@ -266,6 +268,12 @@ class Problem:
         cfg = self._lib.mxp_persist_config(self._h, ct.byref(k))
         return int(cfg), int(k.value)
 
+    def persist_geometry(self):
+        """(txo, tyo, ntx, nty, K) of the persistent kernel's tiles, or None."""
+        v = [ct.c_int(0) for _ in range(5)]
+        cfg = self._lib.mxp_persist_geometry(self._h, *[ct.byref(x) for x in v])
+        return tuple(int(x.value) for x in v) if cfg >= 0 else None
+
     # -- operations (all on the problem's stream)
     def empty(self):
         import torch
@@ -391,6 +399,13 @@ def persist_tile_plan(n0, n1, slots, k, txmax, tymax):
     ok = load().mxp_persist_tile_plan(int(n0), int(n1), int(slots), int(k), int(txmax), int(tymax),
                                       *[ct.byref(v) for v in out])
     return tuple(int(v.value) for v in out) if ok else None
+
+
+def measure_fma_peak(device=0):
+    """(FP32, FP64) fused multiply-add throughput of the device in flop/s."""
+    f32, f64 = ct.c_double(0), ct.c_double(0)
+    _check(load().mxp_measure_fma_peak(int(device), ct.byref(f32), ct.byref(f64)))
+    return float(f32.value), float(f64.value)
 
 
 def kernel_launch_count() -> int:

@@ -56,3 +56,22 @@ def test_invalid_parameters_are_rejected(native):
         assert e.value.status == 1
     with pytest.raises(native.MxpError):
         native.Problem(2, (4, 4), 1, -np.ones(36))
+
+
+def test_timeout_survives_a_later_persistent_launch(native):
+    """The error word of a timed-out wait is kept by the next persistent launch
+    (which used to clear it before starting) until the host reads it; the
+    problem's next action is then correct again."""
+    g = I.Grid(2, (120, 100), 8)
+    c = I.layered_grf(g, seed=I.SEED_BASE + 17, corr_cells=4.0)
+    p = I.paper_params(g, c, ppw=10.0)
+    G = native.Problem.from_grid(g, c, p)
+    G.set_params(prec="c64", exp_tol=1e-6, persist_cfg=6)
+    assert G.persist_config()[0] == 6
+    s = native.load().mxp_selftest_barrier_timeout(G._h)
+    assert s == 7, native.load().mxp_last_error()          # MXP_ETIMEOUT
+    x = torch.from_numpy(I.random_complex(g.n_total, 3)).cuda()
+    got = G.apply_phi(0, x)[0].cpu().numpy()
+    G.set_params(persist_cfg=-2, fuse_k=1)
+    ref = G.apply_phi(0, x)[0].cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 5e-5
