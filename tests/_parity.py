@@ -1,0 +1,88 @@
+"""Element-wise comparison of a GPU result with the oracle's.
+
+Every GPU-vs-oracle check reports three numbers, all relative to max|ref| over
+the whole grid:
+  max_int  the largest |got - ref| over the interior cells,
+  max_pml  the largest |got - ref| over the PML cells (0 when there is no PML),
+  l2       ||got - ref|| / ||ref||.
+A wrong value confined to one tile seam, one PML corner or one ring row moves
+max_int or max_pml by about its own size, whatever the grid size, where the l2
+norm would dilute it.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+
+def pml_mask(grid) -> np.ndarray:
+    """True for unknowns inside the PML of any axis (flat, x fastest)."""
+    m = np.zeros(grid.shape, dtype=bool)
+    p = grid.npml
+    if p == 0:
+        return m.reshape(-1)
+    for ax in range(grid.dim):
+        n = grid.n[ax]
+        idx = np.arange(n)
+        inside = (idx < p) | (idx >= n - p)
+        shape = [1] * grid.dim
+        shape[grid.dim - 1 - ax] = n          # numpy axes are reversed (x fastest)
+        m |= inside.reshape(shape)
+    return m.reshape(-1)
+
+
+def face_mask(grid) -> np.ndarray:
+    """True for the boundary rows of the grid (the cells next to a face), the
+    cells that carry the ghost-point terms of sound-hard / absorbing faces."""
+    m = np.zeros(grid.shape, dtype=bool)
+    for ax in range(grid.dim):
+        n = grid.n[ax]
+        idx = np.arange(n)
+        shape = [1] * grid.dim
+        shape[grid.dim - 1 - ax] = n
+        m |= ((idx == 0) | (idx == n - 1)).reshape(shape)
+    return m.reshape(-1)
+
+
+def errors(got, ref, grid, mask=None) -> dict:
+    """max_pml is taken over `mask` when given (e.g. face_mask), else the PML."""
+    got = np.asarray(got).reshape(-1)
+    ref = np.asarray(ref).reshape(-1)
+    assert got.shape == ref.shape, (got.shape, ref.shape)
+    scale = float(np.max(np.abs(ref)))
+    d = np.abs(got - ref)
+    pm = pml_mask(grid) if mask is None else mask
+    out = {
+        "max_int": float(d[~pm].max() / scale) if (~pm).any() else 0.0,
+        "max_pml": float(d[pm].max() / scale) if pm.any() else 0.0,
+        "l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+    }
+    if not np.all(np.isfinite(got)):
+        out["max_int"] = out["max_pml"] = out["l2"] = float("inf")
+    return out
+
+
+def check(got, ref, grid, tol, l2_tol=None, what="", mask=None) -> dict:
+    """Assert max_int, max_pml <= tol and l2 <= l2_tol (default tol).  With
+    MXP_PARITY_LOG set, every comparison is also appended to that file (one
+    JSON object per line: the measured errors behind the stated bounds)."""
+    e = errors(got, ref, grid, mask)
+    lt = tol if l2_tol is None else l2_tol
+    log = os.environ.get("MXP_PARITY_LOG")
+    if log:
+        with open(log, "a") as fh:
+            fh.write(json.dumps({"what": what, "grid": [grid.dim, list(grid.ni), grid.npml],
+                                 "tol": tol, "l2_tol": lt, **e}) + "\n")
+    assert e["max_int"] <= tol and e["max_pml"] <= tol and e["l2"] <= lt, (what, e, tol, lt)
+    return e
+
+
+# Bounds of the GPU-vs-oracle comparisons.
+TOL_OP = 1e-13        # operator, complex128 (one stencil evaluation)
+TOL_C128 = 1e-10      # exp / psi actions and MatExPre applies, complex128, exp_tol 1e-12
+TOL_SOLUTION = 1e-8   # outer FGMRES solutions at the same outer count, complex128
+TOL_C64 = 2e-4        # complex64 actions at exp_tol 1e-6 against the fp64 oracle
+TOL_BF16S = 8e-2      # bfloat16-storage actions at exp_tol 1e-6 against the fp64 oracle
+TOL_LOW = {"c64": TOL_C64, "bf16s": TOL_BF16S}

@@ -1,12 +1,16 @@
 """Batched solves (several sources per medium advancing in lockstep, one sweep
 launch per pass for the whole batch, sweep sequences replayed from captured
 CUDA graphs): every right-hand side reaches the 1e-6 true residual (checked
-with the oracle's operator) and matches its single-source solve."""
+with the oracle's operator) and matches its single-source solve; in complex128
+the first source of each medium also takes the oracle's outer iteration count
+and its solution agrees with the oracle's element-wise within 1e-8."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2506_03617_gb300 import inputs as I
+
+from _parity import TOL_SOLUTION, check
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,6 +45,7 @@ def test_batch_of_sources_on_two_media(native, prec):
     bs = [torch.from_numpy(b).cuda() for _, b in srcs]
     xs = [probs[k].empty() for k, _ in srcs]
     stats = native.solve_batch(probs, [k for k, _ in srcs], bs, xs, rtol=1e-6, maxit=100)
+    seen = set()
     for (k, b), x, st in zip(srcs, xs, stats):
         assert st["converged"], st
         xh = x.cpu().numpy()
@@ -48,6 +53,12 @@ def test_batch_of_sources_on_two_media(native, prec):
         # agrees with the single-source path to the solve tolerance
         x1, _ = probs[k].solve(torch.from_numpy(b).cuda(), rtol=1e-6)
         assert _rel(xh, x1.cpu().numpy()) < 1e-4
+        if prec == "c128" and k not in seen:
+            # the oracle's Algorithm 1 + FGMRES on the same source
+            seen.add(k)
+            u_ref, info = oracles[k].fgmres(b, rtol=1e-6)
+            assert st["outer_iters"] == info["outer_iters"], (st["outer_iters"], info["outer_iters"])
+            check(xh, u_ref, grids[k], TOL_SOLUTION, what=f"batched solve c128 medium {k}")
 
 
 def test_batch_is_repeatable_with_replayed_graphs(native):

@@ -8,6 +8,8 @@ import pytest
 import oracle
 from paper_2506_03617_gb300 import inputs as I
 
+from _parity import TOL_LOW, check
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -41,18 +43,18 @@ def test_fused3d_matches_unfused_and_oracle(native, grid, prec):
     G.set_params(prec=prec, exp_tol=1e-6, fuse_k=1, tile_cfg=-1)
     assert G.tile_config()[0] == -1
     base = G.apply_phi(0, xd)[0].cpu().numpy()
-    bound = 2e-4 if prec == "c64" else 8e-2
-    assert _rel(base, ref) < bound
+    bound = TOL_LOW[prec]
+    check(base, ref, grid, bound, what=f"3d unfused exp {prec}")
     for cfg in range(N3):
         G.set_params(fuse_k=0, tile_cfg=cfg)
         assert G.tile_config()[0] == cfg
         got = G.apply_phi(0, xd)[0].cpu().numpy()
-        assert _rel(got, ref) < bound, (cfg, _rel(got, ref))
+        check(got, ref, grid, bound, what=f"fused3d cfg {cfg} exp {prec}")
         if prec == "c64":
             assert _rel(got, base) < 5e-5, (cfg, _rel(got, base))
     # psi_1 keeps working on the 3D path (unfused sweeps)
     s = G.apply_phi(1, xd)[0].cpu().numpy()
-    assert _rel(s, P.phi(1, x)[0]) < bound
+    check(s, P.phi(1, x)[0], grid, bound, what=f"3d psi1 {prec}")
 
 
 def test_full_size_288_exp_action_fused_vs_unfused(native):

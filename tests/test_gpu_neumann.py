@@ -7,6 +7,8 @@ import pytest
 import oracle
 from paper_2506_03617_gb300 import inputs as I
 
+from _parity import TOL_C128, check
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +37,7 @@ def test_neumann_parity_c128(native, nterms):
     r = I.random_complex(g.n_total, 5)
     w, st = G.apply_matexpre(torch.from_numpy(r).cuda())
     assert st["inner_iters"] == nterms
-    assert _rel(w.cpu().numpy(), P.neumann(r, nterms)) < 1e-10
+    check(w.cpu().numpy(), P.neumann(r, nterms), g, TOL_C128, what=f"neumann N={nterms} c128")
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])

@@ -7,6 +7,8 @@ import pytest
 import oracle
 from paper_2506_03617_gb300 import inputs as I
 
+from _parity import TOL_C128, TOL_C64, TOL_SOLUTION, check
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +47,7 @@ def test_psi2_action_parity_c128(native, grid):
     ref, _ = P.phi(2, x)
     got, passes = G.apply_phi(2, _cuda(x))
     assert passes > 0
-    assert _rel(got.cpu().numpy(), ref) < 1e-10
+    check(got.cpu().numpy(), ref, grid, TOL_C128, what="psi2 c128")
 
 
 @pytest.mark.parametrize("fuse_k", [0, 1])
@@ -55,7 +57,7 @@ def test_psi2_action_c64_fused_and_unfused(native, fuse_k):
     x = I.random_complex(grid.n_total, 5)
     ref, _ = P.phi(2, x)
     got, _ = G.apply_phi(2, _cuda(x))
-    assert _rel(got.cpu().numpy(), ref) < 2e-4
+    check(got.cpu().numpy(), ref, grid, TOL_C64, what=f"psi2 c64 fuse_k={fuse_k}")
 
 
 def test_second_formula_fixed_trip_parity_c128(native):
@@ -65,7 +67,7 @@ def test_second_formula_fixed_trip_parity_c128(native):
     ref, it, _ = P.matexpre(r, fixed=3, variant=1)
     got, st = G.apply_matexpre(_cuda(r))
     assert st["inner_iters"] == it == 3
-    assert _rel(got.cpu().numpy(), ref) < 1e-10
+    check(got.cpu().numpy(), ref, grid, TOL_C128, what="second formula fixed 3 c128")
 
 
 def test_second_formula_tolerance_mode_matches_iterations(native):
@@ -75,7 +77,7 @@ def test_second_formula_tolerance_mode_matches_iterations(native):
     ref, it, _ = P.matexpre(r, fprtol=0.08, variant=1)
     got, st = G.apply_matexpre(_cuda(r))
     assert st["inner_iters"] == it
-    assert _rel(got.cpu().numpy(), ref) < 1e-10
+    check(got.cpu().numpy(), ref, grid, TOL_C128, what="second formula tolerance mode c128")
 
 
 def test_second_formula_solve_parity(native):
@@ -90,7 +92,7 @@ def test_second_formula_solve_parity(native):
     x, st = G.solve(_cuda(b), rtol=1e-6)
     assert st["converged"] and info["converged"]
     assert st["outer_iters"] == info["outer_iters"]
-    assert _rel(x.cpu().numpy(), u_ref) < 1e-8
+    check(x.cpu().numpy(), u_ref, grid, TOL_SOLUTION, what="second formula solve c128")
 
 
 @pytest.mark.parametrize("prec", ["c64", "bf16s"])

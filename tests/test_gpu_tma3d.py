@@ -8,6 +8,8 @@ import pytest
 import oracle
 from paper_2506_03617_gb300 import inputs as I
 
+from _parity import TOL_LOW, check
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -41,11 +43,10 @@ def test_tma_sweep_actions_match_oracle(native, grid, prec):
     assert G.sweep_kernel() == "zmarch_tma_3d"
     x = I.random_complex(grid.n_total, 17)
     xd = torch.from_numpy(x).cuda()
-    bound = 2e-4 if prec == "c64" else 8e-2
     for which in (0, 1, 2):
         got = G.apply_phi(which, xd)[0].cpu().numpy()
         ref = P.phi(which, x)[0]
-        assert _rel(got, ref) < bound, (which, _rel(got, ref))
+        check(got, ref, grid, TOL_LOW[prec], what=f"tma3d phi{which} {prec}")
 
 
 def test_odd_x_extent_uses_register_marching(native):
