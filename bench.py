@@ -38,12 +38,27 @@ UNIT = "Gpts/s"
 L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes per unknown of one exp-action Horner sweep: read p, y, kappa; write p
 BYTES_PER_PT = {"c128": 16 + 16 + 8 + 16, "c64": 8 + 8 + 4 + 8, "bf16s": 4 + 4 + 4 + 4}
-# float32 operations per point update of the fused / persistent sweeps (general PML
-# path): 4 complex multiply-adds for the neighbours (30), the diagonal (6), its
-# product with the centre (8), y + i tau q (4)
-FLOPS_PER_PT = 48
-# FP32 pipe peak of a GB300: 152 SMs x 128 lanes x 2 flops (FMA) x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Algorithmic real flops of one point update (one SpMV row inside the Horner
+# recurrence): about 24 in the 2D interior (28 in 3D), where the neighbour
+# coefficients are the real 1/h^2, and about 70 in PML cells, where they are
+# complex.  A grid's figure weights the two by its PML and interior cell counts.
+ALG_FLOPS_INTERIOR = {2: 24.0, 3: 28.0}
+ALG_FLOPS_PML = 70.0
+# floating-point operations the persistent / fused float kernels execute per
+# point update (one code path for every cell): 20 FMA for the complex five-point
+# stencil, 2 for the diagonal, 2 for y + i tau q, 2 flops each
+EXEC_FLOPS_PER_PT = 48
+# FP32 pipe from unit counts and clock, for context: 152 SMs x 128 lanes x 2 x 2.07 GHz
+FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def alg_flops_per_update(grid):
+    """Algorithmic flops per point update of a grid, weighted by its PML and
+    interior cell counts."""
+    import math
+    n = grid.n_total
+    n_int = math.prod(grid.ni)
+    return (ALG_FLOPS_INTERIOR[grid.dim] * n_int + ALG_FLOPS_PML * (n - n_int)) / n
 
 
 def parse_args():
@@ -64,11 +79,15 @@ def parse_args():
                     help="parse an ncu --csv --print-units base log of dram__bytes_read/write.sum "
                          "for KERNEL (persist2d, fused2d or horner_step) and store the DRAM bytes per "
                          "launch with the kernel source hash in profiles/traffic.json; then exit")
-    ap.add_argument("--experiment", choices=["precond", "marmousi", "fused3d", "solve3d"], default=None,
+    ap.add_argument("--experiment", choices=["precond", "marmousi", "fused3d", "solve3d", "c3",
+                                             "precision", "oracle"], default=None,
                     help="run one of the side measurements (one JSON line per case) and exit: "
                          "precond = Algorithm 1 vs P_N vs the psi_2 variant on the 1088^2 "
                          "workload; marmousi = mixed boundary conditions on a Marmousi-shaped "
-                         "grid vs a PML grid of the same size; fused3d = 3D sweep kernels")
+                         "grid vs a PML grid of the same size; fused3d = 3D sweep kernels; "
+                         "c3 = 288^3 solves in FP64, complex64 and bf16 storage; precision = "
+                         "errors of the low-precision solves against the FP64 oracle (c1) and "
+                         "the FP64 GPU path (c2); oracle = timed oracle runs on the host cores")
     ap.add_argument("--persist-cfg", type=int, default=None,
                     help="with --profile-case 2d: force this persistent-kernel configuration "
                          "(skips the autotuner's other candidates)")
@@ -356,10 +375,13 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel: the exp-action sweeps (>= 90% of the
     # solve's sweeps); timed live here with CUDA events on the solve stream
+    fp32_peak, fp64_peak = (v / 1e12 for v in N.measure_fma_peak(dev))
     xr = torch.from_numpy(np.random.default_rng(3).standard_normal(n) + 0j).to(f"cuda:{dev}")
     yr = prob.empty()
     pcfg, ptiles = prob.persist_config()
     tcfg, tk = prob.tile_config()
+    pgeo = prob.persist_geometry()
+    alg_fpu = alg_flops_per_update(grid)
     with torch.cuda.stream(stream):
         prob.apply_phi(0, xr, out=yr)
         torch.cuda.synchronize()
@@ -378,18 +400,30 @@ def run_ours(args):
         # persistent (one launch per action) or fused (K steps per launch) sweeps
         # keep the 1088^2 vectors on chip / in L2: bound by the SM, not by HBM
         nlaunch = 1 if pcfg >= 0 else max(1, passes // max(tk, 1))
-        flops_launch = FLOPS_PER_PT * n * passes / nlaunch
+        flops_launch = alg_fpu * n * passes / nlaunch
         achieved = flops_launch / (t_act / nlaunch) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+        executed = None
+        if pcfg >= 0 and pgeo:
+            txo, tyo, ntx, nty, kk = pgeo
+            upd = ntx * nty * (txo + 2 * kk) * (tyo + 2 * kk) * passes
+            executed = {"flops_per_update": EXEC_FLOPS_PER_PT, "updates_per_launch": upd,
+                        "useful_updates_per_launch": n * passes,
+                        "redundant_ring_fraction": 1.0 - n * passes / upd,
+                        "tflops": EXEC_FLOPS_PER_PT * upd / t_act / 1e12,
+                        "tiles": [txo, tyo, ntx, nty], "k": kk}
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                     "traffic": recorded_traffic("persist2d" if pcfg >= 0 else "fused2d", args.prec),
                     "kernel": (f"k_persist2d cfg {pcfg} ({ptiles} tiles, one launch per exp action)"
                                if pcfg >= 0 else f"k_fused2d cfg {tcfg} (K={tk} steps per launch)"),
-                    "flops_per_launch": flops_launch, "launch_us": t_act / nlaunch * 1e6,
-                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                    "alg_flops_per_update": alg_fpu, "flops_per_launch": flops_launch,
+                    "launch_us": t_act / nlaunch * 1e6,
+                    "peak_kind": "measured FP32 FMA throughput (mxp_measure_fma_peak), of measured",
+                    "peak_derived": FP32_DERIVED_TFLOPS, "executed": executed,
                     "hbm_equivalent_gbs": BYTES_PER_PT[args.prec] * n * passes / t_act / 1e9,
-                    "note": "per-sweep unfused bytes / time; the 1088^2 working set is L2/SM "
-                            "resident, so the HBM roofline applies to the 3D line"}
+                    "note": "algorithmic flops: 24 per interior and 70 per PML point update, "
+                            "weighted over the grid; the 1088^2 working set is L2/SM resident, "
+                            "so the HBM roofline applies to the 3D line"}
     else:
         bytes_launch = BYTES_PER_PT[args.prec] * n
         achieved = bytes_launch / (t_act / passes) / 1e9
@@ -421,11 +455,32 @@ def run_ours(args):
         t3 = ev0.elapsed_time(ev1) / 1e3
         sw3 = t3 / ps3
         a3 = BYTES_PER_PT[args.prec] * g3.n_total / sw3 / 1e9
+        # one whole MatExPre apply (psi_1 action, inner GMRES on exp actions, the
+        # FP64 Krylov vectors) and one solve of the 288^3 point-source problem
+        b3 = torch.from_numpy(I.rhs_from_source(I.gaussian_source(g3)).ravel()).to(f"cuda:{dev}")
+        r3 = b3 / torch.linalg.vector_norm(b3)
+        with torch.cuda.stream(P3.stream):
+            P3.apply_matexpre(r3, out=y3)
+            torch.cuda.synchronize()
+            ev0.record(P3.stream)
+            _, ast = P3.apply_matexpre(r3, out=y3)
+            ev1.record(P3.stream)
+            ev1.synchronize()
+        tm3 = ev0.elapsed_time(ev1) / 1e3
+        am3 = BYTES_PER_PT[args.prec] * g3.n_total * ast["stencil_passes"] / tm3 / 1e9
+        row3 = _timed_solve(P3, b3, maxit=300)
         extra["hbm_resident_3d"] = {
-            "workload": "3d_homogeneous_288 (256^3 + 16-cell PML), one exp action",
-            "gpts": g3.n_total * ps3 / t3 / 1e9, "sweeps": ps3, "achieved_gbs": a3,
-            "frac": a3 / peak}
-        del P3, x3, y3
+            "workload": "3d_homogeneous_288 (256^3 + 16-cell PML)",
+            "exp_action": {"gpts": g3.n_total * ps3 / t3 / 1e9, "sweeps": ps3, "achieved_gbs": a3,
+                           "frac": a3 / peak},
+            "matexpre_apply": {"seconds": tm3, "sweeps": ast["stencil_passes"],
+                               "inner_iters": ast["inner_iters"],
+                               "gpts": g3.n_total * ast["stencil_passes"] / tm3 / 1e9,
+                               "sweep_bytes_gbs": am3, "frac": am3 / peak,
+                               "note": "sweep bytes (28 B per c64 point update) over the whole "
+                                       "apply's time, Krylov work included in the time"},
+            "solve": row3, "kernel": P3.sweep_kernel()}
+        del P3, x3, y3, b3, r3
         torch.cuda.empty_cache()
         # many sources per medium in lockstep (one sweep launch per pass for the batch)
         gb_ = I.Grid(2, (512, 512), 16)
@@ -456,15 +511,51 @@ def run_ours(args):
             "max_true_relres": max(q["true_relres"] for q in bst)}
         del PB
         if not args.no_fp64_compare and args.prec != "c128":
+            # the plain FP64 path on the same problem, and the other low-precision
+            # storage; errors of the low-precision solutions against the FP64 one
+            x_lo = x.clone()
             prob.set_params(prec="c128", exp_tol=1e-12)
-            t0 = time.perf_counter()
-            _, st64 = prob.solve(b, x, rtol=rtol, maxit=300)
-            t64 = time.perf_counter() - t0
+            x64 = prob.empty()
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            _, st64 = prob.solve(b, x64, rtol=rtol, maxit=300)
+            ev1.record(stream)
+            ev1.synchronize()
+            t64 = ev0.elapsed_time(ev1) / 1e3
+            pts64 = st64["pt_updates"]
+            fl64 = alg_fpu * pts64 / t64 / 1e12
+            nrm64 = float(torch.linalg.vector_norm(x64))
             extra["fp64_solve"] = {"seconds": t64,
                                    "outer": st64["outer_iters"],
                                    "inner": st64["inner_iters_total"],
                                    "true_relres": st64["true_relres"],
-                                   "speedup_of_this_precision": t64 / (total_max / args.steps)}
+                                   "pt_updates": pts64, "gpts": pts64 / t64 / 1e9,
+                                   "alg_tflops": fl64, "dfma_peak_tflops": fp64_peak,
+                                   "frac_of_dfma_peak": fl64 / fp64_peak,
+                                   "roofline_note": "FP64 sweeps on an L2-resident grid: bound by "
+                                                    "the FP64 pipe (measured DFMA throughput, of measured)",
+                                   "speedup_of_this_precision": t64 / (total_max / args.steps),
+                                   f"{args.prec}_solution_rel_err":
+                                       float(torch.linalg.vector_norm(x_lo - x64)) / nrm64}
+            other = "bf16s" if args.prec == "c64" else "c64"
+            prob.set_params(prec=other, exp_tol=1e-6)
+            xo = prob.empty()
+            prob.solve(b, xo, rtol=rtol, maxit=300)                # tuning and first launches
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            _, sto = prob.solve(b, xo, rtol=rtol, maxit=300)
+            ev1.record(stream)
+            ev1.synchronize()
+            to = ev0.elapsed_time(ev1) / 1e3
+            extra[f"{other}_solve"] = {"seconds": to, "outer": sto["outer_iters"],
+                                       "inner": sto["inner_iters_total"],
+                                       "true_relres": sto["true_relres"],
+                                       "gpts": sto["pt_updates"] / to / 1e9,
+                                       "speedup_over_fp64": t64 / to,
+                                       "solution_rel_err_vs_fp64":
+                                           float(torch.linalg.vector_norm(xo - x64)) / nrm64}
+            del x64, xo, x_lo
             prob.set_params(prec=args.prec, exp_tol=1e-6)
 
     cpu = None
@@ -518,11 +609,11 @@ def run_profile_case(args):
     return 0
 
 
-def _timed_solve(prob, b, rtol=1e-6, maxit=300):
+def _timed_solve(prob, b, rtol=1e-6, maxit=300, x=None):
     """One solve timed with CUDA events on the problem's stream; the true
     relative residual is recomputed with the FP64 operator."""
     import torch
-    x = prob.empty()
+    x = prob.empty() if x is None else x
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(prob.stream)
@@ -576,6 +667,104 @@ def run_experiment(args):
                               "inner_per_outer": row["inner_total"] / max(row["outer"], 1),
                               **row}), flush=True)
             prob.close()
+    elif args.experiment == "c3":
+        # 256^3 + 16 PML (288^3 unknowns), homogeneous and converging lens, point
+        # source at the centre: FP64, complex64 and bf16-storage actions inside
+        # FP64 FGMRES; low-precision solutions against the FP64 one
+        for name, (g, c, p) in (("3d_homogeneous_288", I.config_3d_homogeneous()),
+                                ("3d_lens_288", I.config_3d_lens())):
+            b = torch.from_numpy(I.rhs_from_source(I.gaussian_source(g)).ravel()).cuda()
+            prob = N.Problem.from_grid(g, c, p)
+            sols = {}
+            for pr in ("c64", "bf16s", "c128"):
+                prob.set_params(prec=pr, exp_tol=1e-12 if pr == "c128" else 1e-6)
+                if pr != "c128":
+                    _timed_solve(prob, b, maxit=2)
+                x = prob.empty()
+                row = _timed_solve(prob, b, maxit=400, x=x)
+                sols[pr] = x
+                row["kernel"] = prob.sweep_kernel()
+                row["gpts"] = g.n_total * row["sweeps"] / row["seconds"] / 1e9
+                print(json.dumps({"experiment": "c3", "workload": name, "prec": pr,
+                                  "unknowns": g.n_total, **row}), flush=True)
+            ref = sols["c128"]
+            nr = float(torch.linalg.vector_norm(ref))
+            for pr in ("c64", "bf16s"):
+                print(json.dumps({"experiment": "c3", "workload": name, "prec": pr,
+                                  "solution_rel_err_vs_fp64_gpu":
+                                      float(torch.linalg.vector_norm(sols[pr] - ref)) / nr}), flush=True)
+            del prob, sols, ref, b
+            torch.cuda.empty_cache()
+    elif args.experiment == "precision":
+        # pattern (1): error of each precision's solution against the FP64
+        # oracle's (c1, where the oracle solves in seconds) and against the FP64
+        # GPU solution (c2, whose own parity with the oracle is tested at 1e-8 on
+        # smaller grids)
+        import oracle
+        import numpy as np
+        g, c, p = I.config_2d_homogeneous()
+        bh = I.rhs_from_source(I.gaussian_source(g)).ravel()
+        u_ref, info = oracle.Problem.from_grid(g, c, p).fgmres(bh, rtol=1e-6)
+        b = torch.from_numpy(bh).cuda()
+        prob = N.Problem.from_grid(g, c, p)
+        for pr in ("c128", "c64", "bf16s"):
+            prob.set_params(prec=pr, exp_tol=1e-12 if pr == "c128" else 1e-6)
+            x = prob.empty()
+            row = _timed_solve(prob, b, maxit=400, x=x)
+            xh = x.cpu().numpy()
+            print(json.dumps({"experiment": "precision", "workload": "2d_homogeneous_160 (c1)",
+                              "prec": pr, **row, "oracle_outer": info["outer_iters"],
+                              "rel_err_vs_fp64_oracle": float(np.linalg.norm(xh - u_ref) / np.linalg.norm(u_ref)),
+                              "max_err_vs_fp64_oracle": float(np.max(np.abs(xh - u_ref)) / np.max(np.abs(u_ref)))}),
+                  flush=True)
+        g, c, p, bh = workload()
+        b = torch.from_numpy(bh).cuda()
+        prob = N.Problem.from_grid(g, c, p)
+        sols = {}
+        for pr in ("c128", "c64", "bf16s"):
+            prob.set_params(prec=pr, exp_tol=1e-12 if pr == "c128" else 1e-6)
+            if pr != "c128":
+                _timed_solve(prob, b, maxit=2)
+            x = prob.empty()
+            row = _timed_solve(prob, b, maxit=400, x=x)
+            sols[pr] = x
+            err = {}
+            if pr != "c128":
+                ref = sols["c128"]
+                err = {"rel_err_vs_fp64_gpu": float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref)),
+                       "max_err_vs_fp64_gpu": float((x - ref).abs().max() / ref.abs().max())}
+            print(json.dumps({"experiment": "precision", "workload": "2d_layered_1088 (c2)", "prec": pr,
+                              **row, **err}), flush=True)
+    elif args.experiment == "oracle":
+        # the fp64 C oracle on this machine's host cores: the full c1 solve with
+        # all cores, and one exp action of c1 and of the c2 sample single-threaded
+        import oracle
+        ncores = os.cpu_count() or 1
+        g, c, p = I.config_2d_homogeneous()
+        P = oracle.Problem.from_grid(g, c, p)
+        bh = I.rhs_from_source(I.gaussian_source(g)).ravel()
+        os.environ["OMP_NUM_THREADS"] = str(ncores)
+        t0 = time.perf_counter()
+        _, info = P.fgmres(bh, rtol=1e-6)
+        ts = time.perf_counter() - t0
+        print(json.dumps({"experiment": "oracle", "case": "c1 full FGMRES solve", "threads": ncores,
+                          "seconds": ts, "outer": info["outer_iters"], "spmv": info["spmv"],
+                          "gpts": info["spmv"] * g.n_total / ts / 1e9}), flush=True)
+        x = I.random_complex(g.n_total, 1)
+        for threads in (1, ncores):
+            oracle.set_threads(threads)
+            t0 = time.perf_counter()
+            _, spmv = P.phi(0, x)
+            ta = time.perf_counter() - t0
+            print(json.dumps({"experiment": "oracle", "case": "c1 exp action", "threads": threads,
+                              "seconds": ta, "spmv": spmv, "gpts": spmv * g.n_total / ta / 1e9}), flush=True)
+        g2, c2, p2, _ = workload()
+        for threads in (1, ncores):
+            oracle.set_threads(threads)
+            pts, secs, _ = oracle_sample(g2, c2, p2)
+            print(json.dumps({"experiment": "oracle", "case": "c2 exp action at t/16", "threads": threads,
+                              "seconds": secs, "gpts": pts / secs / 1e9}), flush=True)
+        oracle.set_threads(ncores)
     elif args.experiment == "solve3d":
         # converging-lens medium of Sec. 4 on 128^3 + 16 PML, point-like source at the centre
         g, c, p = I.config_3d_lens(n_interior=128, npml=16)

@@ -97,8 +97,15 @@ def _load():
             lib.orc_neumann.argtypes = [P, ct.c_int, ct.c_int, cd, cd]
             lib.orc_neumann.restype = ct.c_int64
             lib.orc_gmres_plain.restype = ct.c_int
+            lib.orc_set_threads.argtypes = [ct.c_int]
+            lib.orc_set_threads.restype = None
             _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads the oracle's loops use (for timing runs)."""
+    _load().orc_set_threads(int(n))
 
 
 class Problem:

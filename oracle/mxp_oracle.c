@@ -38,6 +38,7 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -609,4 +610,11 @@ int orc_gmres_plain(const orc_problem *P, int shifted, const cplx *b, cplx *x, d
     fgmres_core(n, op_plain, ctx, NULL, NULL, b, x, rtol * vnorm(n, b), restart, maxit, 0, 1,
                 &st, NULL);
     return st.converged ? st.iters : -st.iters;
+}
+
+/* Threads of the parallel loops above (timing runs only; results do not
+ * depend on it beyond the order of the reductions' partial sums). */
+void orc_set_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
 }
