@@ -348,6 +348,81 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
     }
 }
 
+// One Taylor-Horner step over a thread's R rows of its two columns (the body of
+// k_persist2d_x2): all shared loads of a chunk of CH rows are issued before its
+// arithmetic, then the chunk's results are stored.
+template <int R, int CH, int PX, int BXH>
+__device__ __forceinline__ void x2_step_rows(const float2 *__restrict__ src, float2 *__restrict__ dst,
+                                             const float2 *__restrict__ cy, const float2 *__restrict__ ks,
+                                             int r0, int RH, int cx0, int tx, const float2 (&wpx)[2],
+                                             const float2 (&wmx)[2], const float2 (&wcx)[2], float2 zh,
+                                             float tau, const float2 (&y0r)[R], const float2 (&y1r)[R])
+{
+    float4 up = *reinterpret_cast<const float4 *>(src + r0 * PX + cx0 + 2);
+    float4 cen = *reinterpret_cast<const float4 *>(src + (r0 + 1) * PX + cx0 + 2);
+#pragma unroll
+    for (int c = 0; c < R; c += CH) {
+        if (r0 + c >= RH) break;                 // uniform across the row group
+        float4 dn[CH];
+        float2 wl[CH], er[CH], kk[CH];
+        float4 o[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int ry = r0 + c + j;
+            dn[j] = *reinterpret_cast<const float4 *>(src + (ry + 2) * PX + cx0 + 2);
+            wl[j] = src[(ry + 1) * PX + cx0 + 1];
+            er[j] = src[(ry + 1) * PX + cx0 + 4];
+            kk[j] = ks[ry * BXH + tx];
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int ry = r0 + c + j;
+            const float2 wpy = cy[3 * ry], wmy = cy[3 * ry + 1], wcy = cy[3 * ry + 2];
+            const float2 cA = make_float2(cen.x, cen.y), cB = make_float2(cen.z, cen.w);
+            const float2 uA = make_float2(up.x, up.y), uB = make_float2(up.z, up.w);
+            const float2 nA = make_float2(dn[j].x, dn[j].y), nB = make_float2(dn[j].z, dn[j].w);
+            float2 res[2];
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const float2 e_ = l ? er[j] : cB, w_ = l ? cA : wl[j];
+                const float2 n_ = l ? nB : nA, u_ = l ? uB : uA, c_ = l ? cB : cA;
+                const float kv = l ? kk[j].y : kk[j].x;
+                const float dx = fmaf(kv, zh.x, -(wcx[l].x + wcy.x));
+                const float dy = fmaf(kv, zh.y, -(wcx[l].y + wcy.y));
+                // q = wpx e + wmx w + wpy n + wmy u + d c as one FMA chain per component
+                float qx = wpx[l].x * e_.x;
+                qx = fmaf(-wpx[l].y, e_.y, qx);
+                qx = fmaf(wmx[l].x, w_.x, qx);
+                qx = fmaf(-wmx[l].y, w_.y, qx);
+                qx = fmaf(wpy.x, n_.x, qx);
+                qx = fmaf(-wpy.y, n_.y, qx);
+                qx = fmaf(wmy.x, u_.x, qx);
+                qx = fmaf(-wmy.y, u_.y, qx);
+                float qy = wpx[l].x * e_.y;
+                qy = fmaf(wpx[l].y, e_.x, qy);
+                qy = fmaf(wmx[l].x, w_.y, qy);
+                qy = fmaf(wmx[l].y, w_.x, qy);
+                qy = fmaf(wpy.x, n_.y, qy);
+                qy = fmaf(wpy.y, n_.x, qy);
+                qy = fmaf(wmy.x, u_.y, qy);
+                qy = fmaf(wmy.y, u_.x, qy);
+                qx = fmaf(dx, c_.x, qx);
+                qx = fmaf(-dy, c_.y, qx);
+                qy = fmaf(dx, c_.y, qy);
+                qy = fmaf(dy, c_.x, qy);
+                const float2 yv = l ? y1r[c + j] : y0r[c + j];
+                res[l] = make_float2(fmaf(-tau, qy, yv.x), fmaf(tau, qx, yv.y));
+            }
+            o[j] = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
+            up = cen;
+            cen = dn[j];
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+            *reinterpret_cast<float4 *>(dst + (r0 + c + j + 1) * PX + cx0 + 2) = o[j];
+    }
+}
+
 // The same exp / psi_1 action with two adjacent columns per thread.  The east
 // neighbour of the first column and the west neighbour of the second are the
 // other column's centre (registers), the row below comes as one 16-byte load
@@ -452,7 +527,6 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
         y1r[r] = pv[1];
     }
     __syncthreads();
-
     bool alive = true;
     for (int pass = 0; pass < a.npass && alive; ++pass) {
 #pragma unroll 1
@@ -461,68 +535,7 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
             float2 *dst = (s & 1) ? b0 : b1;
             const float tau = a.tau[pass * K + s];
             const int r0 = grp * R;
-            float4 up = *reinterpret_cast<const float4 *>(src + r0 * PX + cx0 + 2);
-            float4 cen = *reinterpret_cast<const float4 *>(src + (r0 + 1) * PX + cx0 + 2);
-#pragma unroll
-            for (int c = 0; c < R; c += CH) {
-                if (r0 + c >= RH) break;
-                float4 dn[CH];
-                float2 wl[CH], er[CH], kk[CH];
-                float4 o[CH];
-#pragma unroll
-                for (int j = 0; j < CH; ++j) {
-                    const int ry = r0 + c + j;
-                    dn[j] = *reinterpret_cast<const float4 *>(src + (ry + 2) * PX + cx0 + 2);
-                    wl[j] = src[(ry + 1) * PX + cx0 + 1];
-                    er[j] = src[(ry + 1) * PX + cx0 + 4];
-                    kk[j] = ks[ry * BXH + tx];
-                }
-#pragma unroll
-                for (int j = 0; j < CH; ++j) {
-                    const int ry = r0 + c + j;
-                    const float2 wpy = cy[3 * ry], wmy = cy[3 * ry + 1], wcy = cy[3 * ry + 2];
-                    const float2 cA = make_float2(cen.x, cen.y), cB = make_float2(cen.z, cen.w);
-                    const float2 uA = make_float2(up.x, up.y), uB = make_float2(up.z, up.w);
-                    const float2 nA = make_float2(dn[j].x, dn[j].y), nB = make_float2(dn[j].z, dn[j].w);
-                    float2 res[2];
-#pragma unroll
-                    for (int l = 0; l < 2; ++l) {
-                        const float2 e_ = l ? er[j] : cB, w_ = l ? cA : wl[j];
-                        const float2 n_ = l ? nB : nA, u_ = l ? uB : uA, c_ = l ? cB : cA;
-                        const float kv = l ? kk[j].y : kk[j].x;
-                        const float dx = fmaf(kv, zh.x, -(wcx[l].x + wcy.x));
-                        const float dy = fmaf(kv, zh.y, -(wcx[l].y + wcy.y));
-                        float qx = wpx[l].x * e_.x;
-                        qx = fmaf(-wpx[l].y, e_.y, qx);
-                        qx = fmaf(wmx[l].x, w_.x, qx);
-                        qx = fmaf(-wmx[l].y, w_.y, qx);
-                        qx = fmaf(wpy.x, n_.x, qx);
-                        qx = fmaf(-wpy.y, n_.y, qx);
-                        qx = fmaf(wmy.x, u_.x, qx);
-                        qx = fmaf(-wmy.y, u_.y, qx);
-                        qx = fmaf(dx, c_.x, qx);
-                        qx = fmaf(-dy, c_.y, qx);
-                        float qy = wpx[l].x * e_.y;
-                        qy = fmaf(wpx[l].y, e_.x, qy);
-                        qy = fmaf(wmx[l].x, w_.y, qy);
-                        qy = fmaf(wmx[l].y, w_.x, qy);
-                        qy = fmaf(wpy.x, n_.y, qy);
-                        qy = fmaf(wpy.y, n_.x, qy);
-                        qy = fmaf(wmy.x, u_.y, qy);
-                        qy = fmaf(wmy.y, u_.x, qy);
-                        qy = fmaf(dx, c_.y, qy);
-                        qy = fmaf(dy, c_.x, qy);
-                        const float2 yv = l ? y1r[c + j] : y0r[c + j];
-                        res[l] = make_float2(fmaf(-tau, qy, yv.x), fmaf(tau, qx, yv.y));
-                    }
-                    o[j] = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
-                    up = cen;
-                    cen = dn[j];
-                }
-#pragma unroll
-                for (int j = 0; j < CH; ++j)
-                    *reinterpret_cast<float4 *>(dst + (r0 + c + j + 1) * PX + cx0 + 2) = o[j];
-            }
+            x2_step_rows<R, CH, PX, BXH>(src, dst, cy, ks, r0, RH, cx0, tx, wpx, wmx, wcx, zh, tau, y0r, y1r);
             if (FACES && (facemask[0] | facemask[1])) {
                 // boundary rows of a ghost-point face: q gains face * p on those cells
 #pragma unroll
@@ -633,8 +646,11 @@ static int cfg_threads(const PCfg &c) { return c.x2 ? c.BX / 2 * c.BG : c.BX * c
 template <typename S, int K, int BX, int BG, int R>
 static void *kernel_ptr() { return (void *)k_persist2d<S, K, BX, BG, R, (R % 4 == 0) ? 4 : 2>; }
 
+template <int R>
+constexpr int chunk_rows() { return (R % 4 == 0) ? 4 : (R % 2 == 0) ? 2 : 1; }
+
 template <typename S, int K, int BX, int BG, int R, bool F>
-static void *kernel_ptr_x2() { return (void *)k_persist2d_x2<S, K, BX / 2, BG, R, (R % 4 == 0) ? 4 : 2, F>; }
+static void *kernel_ptr_x2() { return (void *)k_persist2d_x2<S, K, BX / 2, BG, R, chunk_rows<R>(), F>; }
 
 template <typename S, int K, int BX, int BG, int R>
 static size_t smem_bytes_x2()

@@ -83,6 +83,18 @@ def check(got, ref, grid, tol, l2_tol=None, what="", mask=None) -> dict:
 TOL_OP = 1e-13        # operator, complex128 (one stencil evaluation)
 TOL_C128 = 1e-10      # exp / psi actions and MatExPre applies, complex128, exp_tol 1e-12
 TOL_SOLUTION = 1e-8   # outer FGMRES solutions at the same outer count, complex128
-TOL_C64 = 2e-4        # complex64 actions at exp_tol 1e-6 against the fp64 oracle
-TOL_BF16S = 8e-2      # bfloat16-storage actions at exp_tol 1e-6 against the fp64 oracle
+# complex64 actions at exp_tol 1e-6: float rounding (u = 6e-8) amplified by the
+# Horner partial sums (about e^theta = e^4 per sub-step) and accumulated over
+# S ~ 60 sub-steps as a random walk: sqrt(S) e^4 u ~ 2.5e-5.  Largest measured
+# element-wise error on GB300: 9.9e-6 (TMA 3D sweep).
+TOL_C64 = 3e-5
+# bfloat16 storage (u = 2^-9) at exp_tol 1e-6.  Kernels that keep the vectors
+# in float between halo exchanges (fused 2D and 3D, persistent) round only at
+# pass boundaries: largest measured 0.040.  Kernels that store p in bfloat16
+# after every step (per-point 2D sweep, z-marching and TMA 3D sweeps, face
+# terms on the per-point sweep) accumulate one rounding per step: largest
+# measured 0.082.
+TOL_BF16S = 0.06
+TOL_BF16S_POINTWISE = 0.12
 TOL_LOW = {"c64": TOL_C64, "bf16s": TOL_BF16S}
+TOL_POINTWISE = {"c64": TOL_C64, "bf16s": TOL_BF16S_POINTWISE}

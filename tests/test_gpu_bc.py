@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2506_03617_gb300 import inputs as I
 
-from _parity import TOL_C128, TOL_LOW, TOL_OP, TOL_SOLUTION, check, face_mask, pml_mask
+from _parity import TOL_C128, TOL_LOW, TOL_OP, TOL_POINTWISE, TOL_SOLUTION, check, face_mask, pml_mask
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -89,7 +89,8 @@ def test_low_precision_phi_with_faces(native, prec):
         ref, _ = P.phi(which, x)
         got, _ = G.apply_phi(which, _cuda(x))
         base[which] = got.cpu().numpy()
-        check(base[which], ref, grid, bound, what=f"faces per-point phi{which} {prec}", mask=_mask(grid))
+        check(base[which], ref, grid, TOL_POINTWISE[prec], what=f"faces per-point phi{which} {prec}",
+              mask=_mask(grid))
     ran = set()
     for cfg in range(9):
         G.set_params(persist_cfg=cfg)

@@ -8,7 +8,7 @@ import pytest
 import oracle
 from paper_2506_03617_gb300 import inputs as I
 
-from _parity import TOL_LOW, check
+from _parity import TOL_LOW, TOL_POINTWISE, check
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,7 +47,7 @@ def test_every_tile_config_matches_unfused_and_oracle(native, gi, prec):
         G.set_params(prec=prec, exp_tol=1e-6, fuse_k=1, tile_cfg=-1)
         assert G.tile_config()[0] == -1
         base = G.apply_phi(which, xd)[0].cpu().numpy()
-        check(base, ref, grid, bound, what=f"unfused phi{which} {prec}")
+        check(base, ref, grid, TOL_POINTWISE[prec], what=f"unfused phi{which} {prec}")
         for cfg in range(native.load().mxp_num_tile_configs()):
             G.set_params(fuse_k=0, tile_cfg=cfg)
             assert G.tile_config()[0] == cfg

@@ -8,7 +8,7 @@ import pytest
 import oracle
 from paper_2506_03617_gb300 import inputs as I
 
-from _parity import TOL_LOW, check
+from _parity import TOL_POINTWISE, check
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,7 +46,7 @@ def test_tma_sweep_actions_match_oracle(native, grid, prec):
     for which in (0, 1, 2):
         got = G.apply_phi(which, xd)[0].cpu().numpy()
         ref = P.phi(which, x)[0]
-        check(got, ref, grid, TOL_LOW[prec], what=f"tma3d phi{which} {prec}")
+        check(got, ref, grid, TOL_POINTWISE[prec], what=f"tma3d phi{which} {prec}")
 
 
 def test_odd_x_extent_uses_register_marching(native):
