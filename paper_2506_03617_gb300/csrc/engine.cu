@@ -999,7 +999,7 @@ static int64_t phi_dispatch(mxp_problem *P, int which, const double2 *x, double2
     }
 }
 
-static void apply_op(mxp_problem *P, int shifted, const double2 *x, double2 *y)
+static void apply_op(mxp_problem *P, int shifted, const double2 *x, double2 *y, cudaStream_t st = nullptr)
 {
     StepScalars<double2> sc;
     sc.zfac = make_double2(1.0, shifted ? P->prm.shift_s : 0.0);
@@ -1008,7 +1008,7 @@ static void apply_op(mxp_problem *P, int shifted, const double2 *x, double2 *y)
     sc.gamma = make_double2(0.0, 0.0);
     sc.rho = make_double2(1.0, 0.0);
     set_faces<double2>(P, sc);
-    launch_step<double2>(P->geom, P->coef64, P->kappa64, sc, x, nullptr, nullptr, y, P->stream);
+    launch_step<double2>(P->geom, P->coef64, P->kappa64, sc, x, nullptr, nullptr, y, st ? st : P->stream);
     P->passes += 1;
 }
 
@@ -1018,10 +1018,10 @@ static void apply_op(mxp_problem *P, int shifted, const double2 *x, double2 *y)
 // multi-dot also takes w itself (it is V[j+1]), which gives ||w||^2 for that
 // test without an extra pass.  On GB300 these complex128 passes are bound by
 // the FP64 pipe, so each skipped second pass halves their cost.
-static void arnoldi_step(mxp_problem *P, Arnoldi &a, int j)
+static void arnoldi_step(mxp_problem *P, Arnoldi &a, int j, cudaStream_t on = nullptr)
 {
     const int64_t n = P->ntot;
-    cudaStream_t st = P->stream;
+    cudaStream_t st = on ? on : P->stream;
     double2 *w = a.V + (size_t)(j + 1) * n;
     double2 *col = a.hs.H + (size_t)j * (a.R + 1);
     double *gate = a.hs.scal + 6;
@@ -1653,6 +1653,423 @@ static mxp_status batch_solve(mxp_problem *P, int nr, const double2 *const *b, d
     return MXP_OK;
 }
 
+// ------------------------------------------------------------------ grouped solves
+// Sources of several 2D problems (different grids and media, one precision)
+// advance in lockstep as one group.  Every pass of an exp / psi_1 action is ONE
+// launch of the grouped fused kernel over all (problem, source, tile) items; a
+// device mask switches converged sources off, so the pass sequence of each
+// action type is captured once as a CUDA graph and replayed for every subset of
+// live sources.  The Krylov work (FP64) stays per source on the group's stream.
+// All problems share one Taylor plan, made for the largest norm bound of the
+// group (extra terms only add accuracy); each problem keeps its own t, shift,
+// PML and psi_1 scalars.
+
+struct GroupSource {
+    mxp_problem *P;
+    int local;     // the source's batch slot in its problem
+};
+
+template <typename S>
+static mxp_status group_solve_t(const std::vector<mxp_problem *> &probs, const std::vector<std::vector<int>> &rhs_of,
+                                const void *const *b_dev, void *const *x_dev, const mxp_solve_opts *o,
+                                std::vector<mxp_solve_stats> &out_stats)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    const int np = (int)probs.size();
+    mxp_problem *P0 = probs[0];
+    cudaStream_t st = P0->stream;
+    for (auto *P : probs) CK(cudaStreamSynchronize(P->stream));
+    std::vector<GroupSource> src;
+    std::vector<int> caller, src0(np);
+    for (int p = 0; p < np; ++p) {
+        src0[p] = (int)src.size();
+        for (size_t q = 0; q < rhs_of[p].size(); ++q) {
+            src.push_back({probs[p], (int)q});
+            caller.push_back(rhs_of[p][q]);
+        }
+    }
+    const int ns = (int)src.size();
+    const int R = o->restart;
+    for (int p = 0; p < np; ++p) {
+        CKS(ensure_base(probs[p]));
+        CKS(ensure_batch(probs[p], (int)rhs_of[p].size(), R, probs[p]->prm.inner_restart));
+    }
+    // tile configuration: the largest problem's tuned fused configuration
+    int big = 0;
+    for (int p = 1; p < np; ++p)
+        if (probs[p]->ntot > probs[big]->ntot) big = p;
+    int cfg = probs[big]->fused_cfg;
+    for (int p = 0; p < np && cfg < 0; ++p) cfg = probs[p]->fused_cfg;
+    if (cfg < 0) cfg = 1;
+    const int K = fused2d_cfg_k(cfg);
+    double nu = 0, nua = 0, tol = 1.0, theta = 1e30;
+    for (auto *P : probs) {
+        nu = std::max(nu, P->nu);
+        nua = std::max(nua, P->nu_aug);
+        tol = std::min(tol, P->prm.exp_tol);
+        theta = std::min(theta, theta_of(P));
+    }
+    const TaylorPlan plan[2] = {make_plan(nu, tol, theta, K), make_plan(nua, tol * 0.1, theta, K)};
+    // work items and per-problem tables
+    std::vector<GroupProblem> gp(np);
+    std::vector<int4> bmap;
+    for (int p = 0; p < np; ++p) {
+        mxp_problem *P = probs[p];
+        GroupProblem &g = gp[p];
+        g.n0 = P->geom.n[0];
+        g.n1 = P->geom.n[1];
+        g.npml = P->grid.npml;
+        g.nmax = P->geom.nmax;
+        int ntx = 0, nty = 0;
+        fused2d_tiles(cfg, g.n0, g.n1, P->fused_cfg == cfg ? P->fused_tyo : 0, &g.txo, &g.tyo, &ntx, &nty);
+        g.coef = P->coef32;
+        g.kappa = P->kappa32;
+        for (int i = 0; i < 4; ++i) g.slot[i] = P->bslot[i];
+        g.src0 = src0[p];
+        for (int j = 0; j < (int)rhs_of[p].size(); ++j)
+            for (int by = 0; by < nty; ++by)
+                for (int bx = 0; bx < ntx; ++bx) bmap.push_back(make_int4(p, j, bx, by));
+    }
+    // pass sequences (slot rotation shared by all problems) and their scalars
+    struct Pass { int in, iy, o; };
+    std::vector<Pass> seq[2];
+    std::vector<FusedScalars> sct[2];
+    int fin[2] = {0, 0};
+    for (int w = 0; w < 2; ++w) {
+        const TaylorPlan &pl = plan[w];
+        std::vector<AugScalars> aug;
+        for (auto *P : probs) aug.emplace_back(w, cd(0.0, -P->prm.t * P->mu / pl.S), pl.S);
+        int iy = 0;
+        for (int sub = 0; sub < pl.S; ++sub) {
+            int in = iy;
+            for (auto &a : aug) a.begin_substep();
+            for (int k = pl.m; k >= 1; k -= K) {
+                const int ob = (in == iy) ? (iy + 1) % 3 : 3 - iy - in;
+                seq[w].push_back({in, iy, ob});
+                for (int p = 0; p < np; ++p) {
+                    mxp_problem *P = probs[p];
+                    const cd rho = std::exp(cd(0.0, P->prm.t * P->mu));
+                    FusedStep steps[kMaxFuse];
+                    for (int q = 0; q < K; ++q) {
+                        const int kk = k - q;
+                        const cd gam = aug[p].gamma(kk);
+                        steps[q] = FusedStep{P->prm.t / ((double)pl.S * kk), gam.real(), gam.imag(), rho.real(),
+                                             rho.imag(), (sub == pl.S - 1 && kk == 1) ? 1 : 0};
+                        aug[p].step(kk);
+                    }
+                    FusedScalars fs;
+                    fused2d_scalars(cfg, steps, make_float2(1.0f, (float)P->prm.shift_s), 0.0f,
+                                    (float)(1.0 / (P->grid.h * P->grid.h)), &fs);
+                    sct[w].push_back(fs);
+                }
+                in = ob;
+            }
+            iy = in;
+            for (auto &a : aug) a.end_substep();
+        }
+        fin[w] = iy;
+    }
+    // device copies (freed at the end of the call)
+    GroupProblem *gp_dev = nullptr;
+    int4 *bmap_dev = nullptr;
+    FusedScalars *sc_dev[2] = {nullptr, nullptr};
+    int *active_dev = nullptr;
+    double *hbuf = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    struct Cleanup {
+        std::vector<void *> dev;
+        double *host = nullptr;
+        cudaGraphExec_t *g = nullptr;
+        ~Cleanup()
+        {
+            for (void *d : dev) cudaFree(d);
+            if (host) cudaFreeHost(host);
+            for (int w = 0; w < 2; ++w)
+                if (g[w]) cudaGraphExecDestroy(g[w]);
+        }
+    } cleanup;
+    cleanup.g = graph;
+    CK(cudaMalloc(&gp_dev, np * sizeof(GroupProblem)));
+    cleanup.dev.push_back(gp_dev);
+    CK(cudaMalloc(&bmap_dev, bmap.size() * sizeof(int4)));
+    cleanup.dev.push_back(bmap_dev);
+    for (int w = 0; w < 2; ++w) {
+        CK(cudaMalloc(&sc_dev[w], sct[w].size() * sizeof(FusedScalars)));
+        cleanup.dev.push_back(sc_dev[w]);
+        CK(cudaMemcpyAsync(sc_dev[w], sct[w].data(), sct[w].size() * sizeof(FusedScalars), cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMalloc(&active_dev, ns * sizeof(int)));
+    cleanup.dev.push_back(active_dev);
+    CK(cudaMallocHost(&hbuf, (size_t)ns * 8 * sizeof(double)));
+    cleanup.host = hbuf;
+    CK(cudaMemcpyAsync(gp_dev, gp.data(), np * sizeof(GroupProblem), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(bmap_dev, bmap.data(), bmap.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    const int nblocks = (int)bmap.size();
+    auto launch_passes = [&](int w, cudaStream_t on) {
+        for (size_t q = 0; q < seq[w].size(); ++q)
+            launch_fused2d_group<S>(cfg, gp_dev, bmap_dev, nblocks, sc_dev[w] + q * np, active_dev, seq[w][q].in,
+                                    seq[w][q].iy, w ? 3 : -1, seq[w][q].o, on);
+    };
+    // capture each action type's pass sequence once (private stream; the caller's
+    // stream may be the legacy stream); without capture the passes run directly
+    if (!P0->cap_stream) CK(cudaStreamCreateWithFlags(&P0->cap_stream, cudaStreamNonBlocking));
+    for (int w = 0; w < 2; ++w) {
+        const long long l0 = g_launch_count.load();
+        cudaGraph_t gr = nullptr;
+        bool ok = cudaStreamBeginCapture(P0->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            launch_passes(w, P0->cap_stream);
+            ok = cudaStreamEndCapture(P0->cap_stream, &gr) == cudaSuccess && gr &&
+                 cudaGraphInstantiate(&graph[w], gr, 0) == cudaSuccess;
+            if (gr) cudaGraphDestroy(gr);
+        }
+        if (!ok) {
+            cudaGetLastError();
+            graph[w] = nullptr;
+        }
+        g_launch_count.store(l0);
+    }
+    std::vector<int> active_h(ns, 0);
+    std::vector<int64_t> passes_src(ns, 0);
+    // out[q] = action w of in[q] (or in[q] minus it, out_mode 1) for the listed sources
+    auto phi_group = [&](int w, const std::vector<int> &ids, const std::vector<const double2 *> &in,
+                         const std::vector<double2 *> &out, int out_mode) -> mxp_status {
+        for (size_t q = 0; q < ids.size(); ++q) {
+            const GroupSource &g = src[ids[q]];
+            const int64_t n = g.P->ntot;
+            launch_convert_in<S>(in[q], (S *)g.P->bslot[w ? 3 : 0] + g.local * n, n, st);
+            if (w) CK(cudaMemsetAsync((S *)g.P->bslot[0] + g.local * n, 0, (size_t)n * sizeof(S), st));
+        }
+        std::fill(active_h.begin(), active_h.end(), 0);
+        for (int id : ids) active_h[id] = 1;
+        // pageable source: the copy is staged before the call returns
+        CK(cudaMemcpyAsync(active_dev, active_h.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (graph[w]) {
+            CK(cudaGraphLaunch(graph[w], st));
+            count_launch((int)seq[w].size());
+        } else {
+            launch_passes(w, st);
+        }
+        for (size_t q = 0; q < ids.size(); ++q) {
+            const GroupSource &g = src[ids[q]];
+            const int64_t n = g.P->ntot;
+            launch_convert_out<S>((S *)g.P->bslot[fin[w]] + g.local * n, out[q], in[q], out_mode, n, st);
+            passes_src[ids[q]] += (int64_t)plan[w].S * plan[w].m;
+            g.P->passes += (int64_t)plan[w].S * plan[w].m;
+        }
+        CK(cudaGetLastError());
+        return MXP_OK;
+    };
+    auto rhs_of_src = [&](int id) -> mxp_problem::Rhs & { return src[id].P->rhs[src[id].local]; };
+    auto nof = [&](int id) { return src[id].P->ntot; };
+    auto read_group = [&](const std::vector<int> &ids, bool outer, int first, int cnt) -> mxp_status {
+        for (size_t q = 0; q < ids.size(); ++q) {
+            const Arnoldi &a = outer ? rhs_of_src(ids[q]).outer : rhs_of_src(ids[q]).inner;
+            CK(cudaMemcpyAsync(hbuf + 8 * q, a.hs.scal + first, cnt * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+        return MXP_OK;
+    };
+    // Algorithm 1 for the listed sources in lockstep (inner GMRES capped at the
+    // restart length, as in the single-problem batched form)
+    auto matexpre_group = [&](const std::vector<int> &ids, const std::vector<const double2 *> &in,
+                              const std::vector<double2 *> &out, std::vector<int> &inner_iters) -> mxp_status {
+        const int nb = (int)ids.size();
+        std::vector<double2 *> rts(nb);
+        for (int i = 0; i < nb; ++i) rts[i] = rhs_of_src(ids[i]).rt;
+        CKS(phi_group(1, ids, in, rts, 0));
+        for (int i = 0; i < nb; ++i) {
+            mxp_problem *P = src[ids[i]].P;
+            Arnoldi &a = rhs_of_src(ids[i]).inner;
+            CK(cudaMemsetAsync(out[i], 0, nof(ids[i]) * sizeof(double2), st));
+            krylov_nrm2sq(rts[i], nof(ids[i]), a.hs.scal, P->ks, st);
+            hess_start(a.hs, st);
+            krylov_scale_invnorm(a.V, rts[i], a.hs.scal, nof(ids[i]), st);
+        }
+        CKS(read_group(ids, false, 3, 1));
+        std::vector<double> zeta(nb);
+        std::vector<int> jj(nb, 0);
+        std::vector<char> act(nb, 1);
+        for (int i = 0; i < nb; ++i) {
+            zeta[i] = hbuf[8 * i];
+            if (!std::isfinite(zeta[i])) return fail(MXP_ENAN, "psi_1(i t A_s) r is not finite");
+            if (zeta[i] == 0.0) act[i] = 0;
+        }
+        int jcap = 0;
+        for (int i = 0; i < nb; ++i) jcap = std::max(jcap, src[ids[i]].P->prm.inner_restart);
+        for (int j = 0; j < jcap; ++j) {
+            std::vector<int> live, live_ids;
+            std::vector<const double2 *> vin;
+            std::vector<double2 *> vout;
+            for (int i = 0; i < nb; ++i) {
+                const mxp_problem *P = src[ids[i]].P;
+                const int fixed = P->prm.inner_fixed;
+                const int jmax = std::min(P->prm.inner_restart, fixed > 0 ? fixed : P->prm.inner_maxit);
+                if (!act[i] || j >= jmax) continue;
+                Arnoldi &a = rhs_of_src(ids[i]).inner;
+                live.push_back(i);
+                live_ids.push_back(ids[i]);
+                vin.push_back(a.V + (size_t)j * nof(ids[i]));
+                vout.push_back(a.V + (size_t)(j + 1) * nof(ids[i]));
+            }
+            if (live.empty()) break;
+            CKS(phi_group(0, live_ids, vin, vout, 1));
+            for (int i : live) arnoldi_step(src[ids[i]].P, rhs_of_src(ids[i]).inner, j, st);
+            CK(cudaGetLastError());
+            CKS(read_group(live_ids, false, 1, 2));
+            for (size_t q = 0; q < live.size(); ++q) {
+                const int i = live[q];
+                const mxp_problem *P = src[ids[i]].P;
+                const double est = hbuf[8 * q], brk = hbuf[8 * q + 1];
+                if (!std::isfinite(est)) return fail(MXP_ENAN, "inner GMRES residual is not finite");
+                jj[i] = j + 1;
+                if (brk != 0.0 || (P->prm.inner_fixed <= 0 && est <= P->prm.fprtol * zeta[i])) act[i] = 0;
+            }
+        }
+        for (int i = 0; i < nb; ++i) {
+            inner_iters[i] = jj[i];
+            if (jj[i] == 0) continue;
+            Arnoldi &a = rhs_of_src(ids[i]).inner;
+            hess_backsolve(a.hs, jj[i], st);
+            krylov_maxpy(out[i], a.V, nof(ids[i]), jj[i], a.hs.y, 1.0, nof(ids[i]), st);
+        }
+        CK(cudaGetLastError());
+        return MXP_OK;
+    };
+
+    // outer FGMRES of every source in lockstep
+    std::vector<const double2 *> b(ns);
+    std::vector<double2 *> x(ns);
+    for (int r = 0; r < ns; ++r) {
+        b[r] = (const double2 *)b_dev[caller[r]];
+        x[r] = (double2 *)x_dev[caller[r]];
+    }
+    std::vector<int> all(ns);
+    for (int r = 0; r < ns; ++r) all[r] = r;
+    for (int r = 0; r < ns; ++r) krylov_nrm2sq(b[r], nof(r), rhs_of_src(r).outer.hs.scal, src[r].P->ks, st);
+    CKS(read_group(all, true, 0, 1));
+    std::vector<double> bnorm(ns), relres(ns, 1.0), est(ns, 0.0), secs(ns, 0.0);
+    std::vector<int> total(ns, 0), inner_total(ns, 0), jr(ns, 0);
+    std::vector<char> done(ns, 0), conv(ns, 0);
+    auto now = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+    for (int r = 0; r < ns; ++r) {
+        bnorm[r] = std::sqrt(hbuf[8 * r]);
+        if (!std::isfinite(bnorm[r])) return fail(MXP_ENAN, "right-hand side is not finite");
+        if (!o->x0_given) {
+            CK(cudaMemsetAsync(x[r], 0, nof(r) * sizeof(double2), st));
+            krylov_copy(rhs_of_src(r).r, b[r], nof(r), st);
+        } else {
+            apply_op(src[r].P, 0, x[r], rhs_of_src(r).r, st);
+            krylov_sub(rhs_of_src(r).r, b[r], rhs_of_src(r).r, nof(r), st);
+        }
+        if (bnorm[r] == 0.0) {
+            CK(cudaMemsetAsync(x[r], 0, nof(r) * sizeof(double2), st));
+            done[r] = conv[r] = 1;
+            relres[r] = 0;
+        }
+    }
+    while (true) {
+        std::vector<int> live;
+        for (int r = 0; r < ns; ++r)
+            if (!done[r]) live.push_back(r);
+        if (live.empty()) break;
+        for (int r : live) {
+            Arnoldi &a = rhs_of_src(r).outer;
+            krylov_nrm2sq(rhs_of_src(r).r, nof(r), a.hs.scal, src[r].P->ks, st);
+            hess_start(a.hs, st);
+            krylov_scale_invnorm(a.V, rhs_of_src(r).r, a.hs.scal, nof(r), st);
+        }
+        CKS(read_group(live, true, 3, 1));
+        std::vector<int> cyc;
+        for (size_t q = 0; q < live.size(); ++q) {
+            const int r = live[q];
+            const double beta = hbuf[8 * q];
+            if (!std::isfinite(beta)) return fail(MXP_ENAN, "outer residual is not finite");
+            relres[r] = beta / bnorm[r];
+            jr[r] = 0;
+            if (beta <= o->rtol * bnorm[r]) { done[r] = conv[r] = 1; secs[r] = now(); continue; }
+            if (total[r] >= o->maxit) { done[r] = 1; secs[r] = now(); continue; }
+            cyc.push_back(r);
+        }
+        if (cyc.empty()) continue;
+        std::vector<char> stop(ns, 0);
+        for (int j = 0; j < R; ++j) {
+            std::vector<int> act;
+            for (int r : cyc)
+                if (!stop[r] && total[r] < o->maxit) act.push_back(r);
+            if (act.empty()) break;
+            std::vector<const double2 *> vin;
+            std::vector<double2 *> zout;
+            for (int r : act) {
+                vin.push_back(rhs_of_src(r).outer.V + (size_t)j * nof(r));
+                zout.push_back(rhs_of_src(r).outer.Z + (size_t)j * nof(r));
+            }
+            std::vector<int> inn(act.size(), 0);
+            CKS(matexpre_group(act, vin, zout, inn));
+            for (size_t q = 0; q < act.size(); ++q) {
+                const int r = act[q];
+                inner_total[r] += inn[q];
+                Arnoldi &a = rhs_of_src(r).outer;
+                apply_op(src[r].P, 0, a.Z + (size_t)j * nof(r), a.V + (size_t)(j + 1) * nof(r), st);
+                passes_src[r] += 1;
+                arnoldi_step(src[r].P, a, j, st);
+            }
+            CK(cudaGetLastError());
+            CKS(read_group(act, true, 1, 2));
+            for (size_t q = 0; q < act.size(); ++q) {
+                const int r = act[q];
+                est[r] = hbuf[8 * q];
+                if (!std::isfinite(est[r])) return fail(MXP_ENAN, "outer FGMRES residual is not finite");
+                ++total[r];
+                jr[r] = j + 1;
+                if (hbuf[8 * q + 1] != 0.0 || est[r] <= o->rtol * bnorm[r]) stop[r] = 1;
+            }
+        }
+        for (int r : cyc) {
+            Arnoldi &a = rhs_of_src(r).outer;
+            hess_backsolve(a.hs, jr[r], st);
+            krylov_maxpy(x[r], a.Z, nof(r), jr[r], a.hs.y, 1.0, nof(r), st);
+            apply_op(src[r].P, 0, x[r], rhs_of_src(r).r, st);
+            passes_src[r] += 1;
+            krylov_sub(rhs_of_src(r).r, b[r], rhs_of_src(r).r, nof(r), st);
+            krylov_nrm2sq(rhs_of_src(r).r, nof(r), a.hs.scal + 4, src[r].P->ks, st);
+        }
+        CKS(read_group(cyc, true, 4, 1));
+        for (size_t q = 0; q < cyc.size(); ++q) {
+            const int r = cyc[q];
+            relres[r] = std::sqrt(hbuf[8 * q]) / bnorm[r];
+            if (!std::isfinite(relres[r])) return fail(MXP_ENAN, "true residual is not finite");
+            if (relres[r] <= o->rtol) { done[r] = conv[r] = 1; secs[r] = now(); }
+            else if (total[r] >= o->maxit) { done[r] = 1; secs[r] = now(); }
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    bool all_conv = true;
+    for (int r = 0; r < ns; ++r) {
+        all_conv = all_conv && conv[r];
+        mxp_solve_stats &sr = out_stats[caller[r]];
+        sr.outer_iters = total[r];
+        sr.inner_iters_total = inner_total[r];
+        sr.converged = conv[r];
+        sr.true_relres = relres[r];
+        sr.est_relres = bnorm[r] > 0 ? est[r] / bnorm[r] : 0.0;
+        sr.stencil_passes = passes_src[r];
+        sr.pt_updates = passes_src[r] * nof(r);
+        sr.seconds = secs[r];
+    }
+    if (!all_conv) return fail(MXP_ENOCONV, "outer FGMRES reached maxit for a right-hand side");
+    return MXP_OK;
+}
+
+// Whether a problem can join a grouped solve (2D, complex64 or bf16 storage,
+// zero Dirichlet faces, Algorithm 1).
+static bool groupable(const mxp_problem *P)
+{
+    return P->grid.dim == 2 && (P->prm.prec == MXP_C64 || P->prm.prec == MXP_BF16S) && P->nfaces == 0 &&
+           P->prm.precond == 0;
+}
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -2058,6 +2475,33 @@ mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs, const
     std::vector<mxp_status> status(ng, MXP_OK);
     std::vector<std::string> message(ng);
     std::vector<std::vector<mxp_solve_stats>> stats(ng);
+    // problems that qualify (2D, one low precision, one device, no faces,
+    // Algorithm 1) form one group whose sources advance in lockstep, every pass
+    // one launch over all of them; the others run one host thread each
+    std::vector<size_t> gsel;
+    for (size_t gi = 0; gi < ng; ++gi)
+        if (groupable(handles[gi]) && (gsel.empty() || (handles[gi]->device == handles[gsel[0]]->device &&
+                                                        handles[gi]->prm.prec == handles[gsel[0]]->prm.prec)))
+            gsel.push_back(gi);
+    if (gsel.size() < 2) gsel.clear();
+    std::vector<char> in_group(ng, 0);
+    for (size_t gi : gsel) in_group[gi] = 1;
+    mxp_status group_status = MXP_OK;
+    std::string group_message;
+    std::vector<mxp_solve_stats> group_stats(nrhs > 0 ? nrhs : 1, mxp_solve_stats{});
+    auto run_group = [&]() {
+        std::vector<mxp_problem *> gp;
+        std::vector<std::vector<int>> rof;
+        for (size_t gi : gsel) {
+            gp.push_back(handles[gi]);
+            rof.push_back(groups[gi]);
+        }
+        DeviceGuard guard(gp[0]->device);
+        group_status = (gp[0]->prm.prec == MXP_C64)
+                           ? group_solve_t<float2>(gp, rof, b_dev, x_dev, opts, group_stats)
+                           : group_solve_t<__nv_bfloat162>(gp, rof, b_dev, x_dev, opts, group_stats);
+        if (group_status != MXP_OK) group_message = g_last_error;
+    };
     auto run = [&](size_t gi) {
         mxp_problem *P = handles[gi];
         DeviceGuard guard(P->device);
@@ -2074,14 +2518,24 @@ mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs, const
     if (ng == 1) {
         run(0);
     } else {
-        // different problems (grids, media) run concurrently, one host thread each;
-        // their kernels overlap on the GPU when the problems use different streams
+        // the group and the remaining problems run concurrently, one host thread
+        // each; their kernels overlap on the GPU when they use different streams
         std::vector<std::thread> th;
-        for (size_t gi = 0; gi < ng; ++gi) th.emplace_back(run, gi);
+        if (!gsel.empty()) th.emplace_back(run_group);
+        for (size_t gi = 0; gi < ng; ++gi)
+            if (!in_group[gi]) th.emplace_back(run, gi);
         for (auto &t : th) t.join();
     }
     mxp_status worst = MXP_OK;
+    if (!gsel.empty()) {
+        if (per_rhs)
+            for (size_t gi : gsel)
+                for (int r : groups[gi]) per_rhs[r] = group_stats[r];
+        if (group_status != MXP_OK && group_status != MXP_ENOCONV) return fail(group_status, group_message);
+        if (group_status == MXP_ENOCONV) worst = MXP_ENOCONV;
+    }
     for (size_t gi = 0; gi < ng; ++gi) {
+        if (in_group[gi]) continue;
         if (per_rhs)
             for (size_t q = 0; q < groups[gi].size(); ++q) per_rhs[groups[gi][q]] = stats[gi][q];
         if (status[gi] != MXP_OK && status[gi] != MXP_ENOCONV) return fail(status[gi], message[gi]);

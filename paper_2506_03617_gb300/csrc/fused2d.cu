@@ -21,47 +21,26 @@
 
 namespace mxp {
 
-struct FusedScalars {
-    float2 zfac;      // 1 + i s
-    float mu;
-    float ih2;        // 1 / h^2 (interior coefficient)
-    float tau[kMaxFuse];
-    float2 gamma[kMaxFuse];
-    float2 rho;       // applied after the last step when rho_on
-    int rho_on;
-};
-
+// One tile (bxi, byi) of one vector: the body shared by the single-grid kernel
+// and the grouped kernel.  sm: dynamic shared memory of the block.
 template <typename S, int K, int RX, int RT, int G, bool HAS_V>
-__global__ void __launch_bounds__(RX *G, (RX * G <= 512 && !HAS_V) ? 2 : 1) k_fused2d(int n0, int n1, int npml, int nmax, int TXO,
-                                                   int TYO,
-                                                   const float2 *__restrict__ coef,
-                                                   const float *__restrict__ kappa,
-                                                   const FusedScalars sc,
-                                                   const S *__restrict__ pin,
-                                                   const S *__restrict__ yv_g,
-                                                   const S *__restrict__ v_g,
-                                                   S *__restrict__ pout)
+__device__ __forceinline__ void fused2d_tile(int n0, int n1, int npml, int nmax, int TXO, int TYO, int bxi,
+                                             int byi, const float2 *__restrict__ coef,
+                                             const float *__restrict__ kappa, const FusedScalars &sc,
+                                             const S *__restrict__ pin, const S *__restrict__ yv_g,
+                                             const S *__restrict__ v_g, S *__restrict__ pout, float2 *sm)
 {
     constexpr int RY = RT * G;
     constexpr int PX = RX + 2;                 // padded row (zero column on each side)
     // output tile TXO x TYO (<= RX-2K x RY-2K, chosen at run time); region = tile + K halo
-    extern __shared__ float2 sm[];
-    // blockIdx.z selects one vector of a batch (vectors of one grid, n0*n1 apart)
-    {
-        const int64_t off = (int64_t)blockIdx.z * n0 * n1;
-        pin += off;
-        yv_g += off;
-        if (HAS_V) v_g += off;
-        pout += off;
-    }
     float2 *buf0 = sm;
     float2 *buf1 = sm + (RY + 2) * PX;
     float2 *cy = buf1 + (RY + 2) * PX;         // [RY][2]: wp_y, wm_y of each region row
 
     const int tx = threadIdx.x % RX;
     const int grp = threadIdx.x / RX;
-    const int gx0 = blockIdx.x * TXO - K;
-    const int gy0 = blockIdx.y * TYO - K;
+    const int gx0 = bxi * TXO - K;
+    const int gy0 = byi * TYO - K;
     const int gx = gx0 + tx;
     const bool inx = (gx >= 0) && (gx < n0);
     const bool interior = (gx0 >= npml) && (gx0 + TXO + 2 * K <= n0 - npml) && (gy0 >= npml) &&
@@ -182,6 +161,52 @@ __global__ void __launch_bounds__(RX *G, (RX * G <= 512 && !HAS_V) ? 2 : 1) k_fu
     }
 }
 
+template <typename S, int K, int RX, int RT, int G, bool HAS_V>
+__global__ void __launch_bounds__(RX *G, (RX * G <= 512 && !HAS_V) ? 2 : 1) k_fused2d(int n0, int n1, int npml, int nmax, int TXO,
+                                                   int TYO,
+                                                   const float2 *__restrict__ coef,
+                                                   const float *__restrict__ kappa,
+                                                   const FusedScalars sc,
+                                                   const S *__restrict__ pin,
+                                                   const S *__restrict__ yv_g,
+                                                   const S *__restrict__ v_g,
+                                                   S *__restrict__ pout)
+{
+    extern __shared__ float2 sm[];
+    // blockIdx.z selects one vector of a batch (vectors of one grid, n0*n1 apart)
+    const int64_t off = (int64_t)blockIdx.z * n0 * n1;
+    fused2d_tile<S, K, RX, RT, G, HAS_V>(n0, n1, npml, nmax, TXO, TYO, blockIdx.x, blockIdx.y, coef, kappa, sc,
+                                         pin + off, yv_g + off, HAS_V ? v_g + off : v_g, pout + off, sm);
+}
+
+// The same pass for a group of grids of different sizes in one launch: block b
+// takes the work item bmap[b] = (problem, source of that problem, tile x, tile
+// y); a block whose source has converged (active[source] == 0) returns at
+// once, so one captured launch sequence serves every subset of live sources.
+// The scalars of the pass differ per problem (t, the shift and the psi_1
+// coefficients depend on the grid); slot indices select the problem's batch
+// buffers (its sources' vectors n0 * n1 apart).
+template <typename S, int K, int RX, int RT, int G, bool HAS_V>
+__global__ void __launch_bounds__(RX *G, (RX * G <= 512 && !HAS_V) ? 2 : 1)
+    k_fused2d_group(const GroupProblem *__restrict__ gp, const int4 *__restrict__ bmap,
+                    const FusedScalars *__restrict__ sc_tab, const int *__restrict__ active, int iin, int iy,
+                    int iv, int iout)
+{
+    extern __shared__ float2 sm[];
+    const int4 m = bmap[blockIdx.x];
+    const GroupProblem &P = gp[m.x];
+    if (active[P.src0 + m.y] == 0) return;         // uniform over the block
+    const int n0 = P.n0, n1 = P.n1;
+    const int64_t off = (int64_t)m.y * n0 * n1;
+    const S *pin = static_cast<const S *>(P.slot[iin]) + off;
+    const S *yv = static_cast<const S *>(P.slot[iy]) + off;
+    const S *v = HAS_V ? static_cast<const S *>(P.slot[iv]) + off : nullptr;
+    S *pout = static_cast<S *>(P.slot[iout]) + off;
+    const FusedScalars &sc = sc_tab[m.x];
+    fused2d_tile<S, K, RX, RT, G, HAS_V>(n0, n1, P.npml, P.nmax, P.txo, P.tyo, m.z, m.w, P.coef, P.kappa, sc,
+                                         pin, yv, v, pout, sm);
+}
+
 struct TileCfg {
     int K, RX, RT, G;
 };
@@ -269,6 +294,98 @@ bool launch_fused2d(int cfg, int tyo, const Geom &g, int npml, const float2 *coe
     }
     return true;
 }
+
+void fused2d_scalars(int cfg, const FusedStep *steps, float2 zfac, float mu, float ih2, FusedScalars *out)
+{
+    FusedScalars &sc = *out;
+    sc.zfac = zfac;
+    sc.mu = mu;
+    sc.ih2 = ih2;
+    sc.rho = make_float2(1.f, 0.f);
+    sc.rho_on = 0;
+    const int K = kCfgs[cfg].K;
+    for (int s = 0; s < kMaxFuse; ++s) {
+        sc.tau[s] = 0.f;
+        sc.gamma[s] = make_float2(0.f, 0.f);
+    }
+    for (int s = 0; s < K; ++s) {
+        sc.tau[s] = (float)steps[s].tau;
+        sc.gamma[s] = make_float2((float)steps[s].gamma_re, (float)steps[s].gamma_im);
+        if (steps[s].rho_on) {
+            sc.rho = make_float2((float)steps[s].rho_re, (float)steps[s].rho_im);
+            sc.rho_on = 1;
+        }
+    }
+}
+
+bool fused2d_tiles(int cfg, int n0, int n1, int tyo, int *txo, int *tyo_out, int *ntx, int *nty)
+{
+    if (cfg < 0 || cfg >= kNumCfgs || n0 < 1 || n1 < 1) return false;
+    const TileCfg c = kCfgs[cfg];
+    const int RY = c.RT * c.G;
+    *ntx = (n0 + c.RX - 2 * c.K - 1) / (c.RX - 2 * c.K);
+    *txo = (n0 + *ntx - 1) / *ntx;
+    if (tyo <= 0 || tyo > RY - 2 * c.K) tyo = RY - 2 * c.K;
+    *tyo_out = tyo;
+    *nty = (n1 + tyo - 1) / tyo;
+    return true;
+}
+
+template <typename S, int K, int RX, int RT, int G, bool HAS_V>
+static void launch_group_one(const GroupProblem *gp, const int4 *bmap, int nblocks, const FusedScalars *sc_tab,
+                             const int *active, int iin, int iy, int iv, int iout, cudaStream_t st)
+{
+    constexpr int RY = RT * G;
+    const size_t smem = (size_t)(2 * (RY + 2) * (RX + 2) + 2 * RY) * sizeof(float2);
+    static std::atomic<bool> configured[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !configured[dev].load()) {
+        cudaFuncSetAttribute(k_fused2d_group<S, K, RX, RT, G, HAS_V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        configured[dev].store(true);
+    }
+    count_launch();
+    k_fused2d_group<S, K, RX, RT, G, HAS_V><<<nblocks, RX * G, smem, st>>>(gp, bmap, sc_tab, active, iin, iy, iv,
+                                                                          iout);
+}
+
+template <typename S, int K, int RX, int RT, int G>
+static void launch_group_v(bool hv, const GroupProblem *gp, const int4 *bmap, int nblocks,
+                           const FusedScalars *sc_tab, const int *active, int iin, int iy, int iv, int iout,
+                           cudaStream_t st)
+{
+    if (hv) launch_group_one<S, K, RX, RT, G, true>(gp, bmap, nblocks, sc_tab, active, iin, iy, iv, iout, st);
+    else launch_group_one<S, K, RX, RT, G, false>(gp, bmap, nblocks, sc_tab, active, iin, iy, iv, iout, st);
+}
+
+template <typename S>
+bool launch_fused2d_group(int cfg, const GroupProblem *gp, const int4 *bmap, int nblocks,
+                          const FusedScalars *sc_tab, const int *active, int iin, int iy, int iv, int iout,
+                          cudaStream_t st)
+{
+    if (cfg < 0 || cfg >= kNumCfgs || nblocks < 1) return false;
+    const bool hv = iv >= 0;
+    if (!hv) iv = 0;
+    switch (cfg) {
+    case 0: launch_group_v<S, 2, 128, 8, 4>(hv, gp, bmap, nblocks, sc_tab, active, iin, iy, iv, iout, st); break;
+    case 1: launch_group_v<S, 4, 128, 8, 4>(hv, gp, bmap, nblocks, sc_tab, active, iin, iy, iv, iout, st); break;
+    case 2: launch_group_v<S, 8, 128, 8, 4>(hv, gp, bmap, nblocks, sc_tab, active, iin, iy, iv, iout, st); break;
+    case 3: launch_group_v<S, 4, 64, 4, 8>(hv, gp, bmap, nblocks, sc_tab, active, iin, iy, iv, iout, st); break;
+    case 4: launch_group_v<S, 2, 64, 4, 8>(hv, gp, bmap, nblocks, sc_tab, active, iin, iy, iv, iout, st); break;
+    case 5: launch_group_v<S, 8, 128, 12, 4>(hv, gp, bmap, nblocks, sc_tab, active, iin, iy, iv, iout, st); break;
+    case 6: launch_group_v<S, 4, 128, 4, 4>(hv, gp, bmap, nblocks, sc_tab, active, iin, iy, iv, iout, st); break;
+    case 7: launch_group_v<S, 6, 128, 8, 4>(hv, gp, bmap, nblocks, sc_tab, active, iin, iy, iv, iout, st); break;
+    default: return false;
+    }
+    return true;
+}
+
+template bool launch_fused2d_group<float2>(int, const GroupProblem *, const int4 *, int, const FusedScalars *,
+                                           const int *, int, int, int, int, cudaStream_t);
+template bool launch_fused2d_group<__nv_bfloat162>(int, const GroupProblem *, const int4 *, int,
+                                                   const FusedScalars *, const int *, int, int, int, int,
+                                                   cudaStream_t);
 
 template bool launch_fused2d<float2>(int, int, const Geom &, int, const float2 *, const float *,
                                      const FusedStep *, const float2, float, float, const float2 *,

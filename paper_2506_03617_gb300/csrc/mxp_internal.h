@@ -153,6 +153,37 @@ struct FusedStep {
     double tau, gamma_re, gamma_im, rho_re, rho_im;
     int rho_on;
 };
+// Scalars of one fused pass as the kernels read them.
+struct FusedScalars {
+    float2 zfac;      // 1 + i s
+    float mu;
+    float ih2;        // 1 / h^2 (interior coefficient)
+    float tau[kMaxFuse];
+    float2 gamma[kMaxFuse];
+    float2 rho;       // applied after the last step when rho_on
+    int rho_on;
+};
+void fused2d_scalars(int cfg, const FusedStep *steps, float2 zfac, float mu, float ih2, FusedScalars *out);
+// Tile plan of configuration cfg on an n0 x n1 grid (tyo <= 0: the largest height).
+bool fused2d_tiles(int cfg, int n0, int n1, int tyo, int *txo, int *tyo_out, int *ntx, int *nty);
+// One problem of a grouped pass (fused2d.cu): its grid, coefficient table,
+// kappa, tile plan, the four batch slots (its sources' vectors n0 * n1 apart)
+// and the global index of its first source in the group's active mask.
+struct GroupProblem {
+    int n0, n1, npml, nmax, txo, tyo;
+    const float2 *coef;
+    const float *kappa;
+    void *slot[4];
+    int src0;
+};
+// One launch of a fused pass over every (problem, source, tile) item of a group:
+// bmap[b] = (problem, source of the problem, tile x, tile y); sc_tab[p] = the
+// pass scalars of problem p; active[src0 + source] == 0 skips the item.  iv < 0:
+// no psi source term.
+template <typename S>
+bool launch_fused2d_group(int cfg, const GroupProblem *gp, const int4 *bmap, int nblocks,
+                          const FusedScalars *sc_tab, const int *active, int iin, int iy, int iv, int iout,
+                          cudaStream_t st);
 int fused2d_num_cfgs();
 int fused2d_cfg_k(int cfg);
 int fused2d_cfg_max_tyo(int cfg);
@@ -246,6 +277,26 @@ void hess_update(const HessState &hs, int j, cudaStream_t st);
 void hess_start(const HessState &hs, cudaStream_t st);
 // Solve the j x j upper-triangular system H y = g into hs.y.
 void hess_backsolve(const HessState &hs, int j, cudaStream_t st);
+
+// Tensor-core (tcgen05) forward 3x3 convolution of the learned stage (conv_tc.cu):
+// stride S (1 or 2), input nearest-upsampled by 2 when UPS, Cout <= 64;
+// *err receives 1 when a bounded wait gives up.  Returns false for an
+// unsupported shape.
+bool conv_fwd_tc(int S, int UPS, const float *in, int N, int Cin, int Hs, int Ws, const __nv_bfloat16 *w,
+                 const float *bias, int Cout, int Ho, int Wo, int relu, const float *skip, float *out,
+                 float *out_skip, unsigned *err, cudaStream_t st);
+
+// Tensor-core input gradient of a 3x3 convolution of stride S (conv_tc.cu):
+// gin [N][Cin][Hl][Wl] from gout [N][Cout][Ho][Wo] and the layer's weights
+// W [Cout][Cin][3][3]; Cin <= 64.
+bool conv_bwd_data_tc(int S, const float *gout, int N, int Cout, int Ho, int Wo, const __nv_bfloat16 *w, int Cin,
+                      int Hl, int Wl, float *gin, unsigned *err, cudaStream_t st);
+
+// Tensor-core weight gradient of a 3x3 convolution (conv_tc.cu): gw [Cout][Cin * 9]
+// = sum over pixels of im2col(x) x g (x the layer input [N][Cin][Hs][Ws], upsampled
+// when UPS; g the output gradient [N][Cout][Ho][Wo]); Cout <= 64.  Overwrites gw.
+bool conv_wgrad_tc(int S, int UPS, const float *x, int N, int Cin, int Hs, int Ws, const float *g, int Cout, int Ho,
+                   int Wo, float *gw, unsigned *err, cudaStream_t st);
 
 // Learned stage: z = network(v) on a 2D grid (n0 x n1), see cnn.cu.
 mxp_status cnn_apply_vector(mxp_cnn *net, int n0, int n1, const double2 *v, double vnorm,

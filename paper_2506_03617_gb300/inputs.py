@@ -228,6 +228,31 @@ def config_3d_lens(n_interior: int = 256, npml: int = 16):
     return g, c, paper_params(g, c, ppw=10.0)
 
 
+def config_batched_2d(sources_per_medium: int = 8):
+    """The multi-source batch on mixed 2D grids: eight seeded layered + GRF media
+    (as the 2D layered workload, ppw 8), three of 256^2 and three of 512^2
+    interior cells with a 16-cell PML and two of 1024^2 with a 32-cell PML, each
+    with `sources_per_medium` Gaussian sources at seeded interior positions (64
+    sources in all).  Returns a list of (grid, c, params, centres)."""
+    sizes = [(256, 16)] * 3 + [(512, 16)] * 3 + [(1024, 32)] * 2
+    out = []
+    for i, (n, p) in enumerate(sizes):
+        g = Grid(2, (n, n), p)
+        c = layered_grf(g, SEED_BASE + 3000 + i)
+        out.append((g, c, paper_params(g, c, ppw=8.0),
+                    random_centers(g, sources_per_medium, seed=SEED_BASE + 3100 + i)))
+    return out
+
+
+def config_batched_3d(n_interior: int = 400, npml: int = 16, sources: int = 8):
+    """The 3D part of the multi-source batch: a seeded layered + GRF medium on
+    400^3 interior cells with a 16-cell PML (432^3 unknowns), ppw 8, with
+    `sources` Gaussian sources at seeded interior positions."""
+    g = Grid(3, (n_interior,) * 3, npml)
+    c = layered_grf(g, SEED_BASE + 3200)
+    return g, c, paper_params(g, c, ppw=8.0), random_centers(g, sources, seed=SEED_BASE + 3300)
+
+
 # ---- learned preconditioning stage: seeded initial weights ----
 
 CNN_LAYERS = [  # (c_in, c_out, stride, upsample_input, relu), input order of the flat vector

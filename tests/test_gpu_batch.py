@@ -111,3 +111,55 @@ def test_uneven_problems_solve_concurrently_on_their_own_streams(native):
         torch.cuda.synchronize()
         for i, x1 in zip(mine, xs1):
             assert _rel(xs[i].cpu().numpy(), x1.cpu().numpy()) < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["c64", "bf16s"])
+def test_grouped_solve_of_mixed_grid_sizes(native, prec):
+    """Three media of different grid sizes in one mxp_solve_batch call form one
+    group: every pass of every action is one launch over all (problem, source,
+    tile) items, converged sources are switched off by a device mask.  Each
+    source reaches the 1e-6 true residual of the oracle's operator, the first
+    source of each medium agrees with the oracle's FP64 solution within 1e-5,
+    every source agrees with its problem solved alone, and the group needs far
+    fewer kernel launches than the problems one after another."""
+    grids = [I.Grid(2, (96, 80), 10), I.Grid(2, (64, 64), 8), I.Grid(2, (48, 40), 6)]
+    probs, oracles, srcs = [], [], []
+    for k, g in enumerate(grids):
+        c = I.layered_grf(g, seed=I.SEED_BASE + 4400 + k, corr_cells=4.0)
+        p = I.paper_params(g, c, ppw=10.0)
+        G = native.Problem.from_grid(g, c, p)
+        G.set_params(prec=prec, exp_tol=1e-6)
+        probs.append(G)
+        oracles.append(oracle.Problem.from_grid(g, c, p))
+        for ctr in I.random_centers(g, 3, seed=I.SEED_BASE + 4500 + k):
+            srcs.append((k, I.rhs_from_source(I.gaussian_source(g, center=ctr)).ravel()))
+    order = [3, 0, 6, 1, 4, 7, 2, 5, 8]                 # interleaved across problems
+    srcs = [srcs[i] for i in order]
+    bs = [torch.from_numpy(b).cuda() for _, b in srcs]
+    xs = [probs[k].empty() for k, _ in srcs]
+    l0 = native.kernel_launch_count()
+    stats = native.solve_batch(probs, [k for k, _ in srcs], bs, xs, rtol=1e-6, maxit=100)
+    torch.cuda.synchronize()
+    grouped_launches = native.kernel_launch_count() - l0
+    seen = set()
+    for (k, b), x, st in zip(srcs, xs, stats):
+        assert st["converged"], st
+        assert st["seconds"] > 0 and st["stencil_passes"] > 0
+        xh = x.cpu().numpy()
+        assert np.linalg.norm(b - oracles[k].apply(xh)) / np.linalg.norm(b) <= 1.000001e-6
+        if k not in seen:
+            seen.add(k)
+            u_ref, _ = oracles[k].fgmres(b, rtol=1e-6)
+            check(xh, u_ref, grids[k], 1e-5, what=f"grouped solve {prec} medium {k}")
+    # each problem alone (the single-problem lockstep path)
+    alone = 0
+    for k in range(3):
+        mine = [i for i, (kk, _) in enumerate(srcs) if kk == k]
+        xs1 = [probs[k].empty() for _ in mine]
+        l1 = native.kernel_launch_count()
+        native.solve_batch([probs[k]], [0] * len(mine), [bs[i] for i in mine], xs1, rtol=1e-6, maxit=100)
+        torch.cuda.synchronize()
+        alone += native.kernel_launch_count() - l1
+        for i, x1 in zip(mine, xs1):
+            assert _rel(xs[i].cpu().numpy(), x1.cpu().numpy()) < 1e-4
+    assert grouped_launches < 0.8 * alone, (grouped_launches, alone)
