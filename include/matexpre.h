@@ -344,6 +344,28 @@ mxp_status mxp_cnn_backward(mxp_cnn *net, const float *x_dev, const float *gy_de
 mxp_status mxp_cnn_train_step(mxp_cnn *net, int N, int H, int W, const float *x_dev,
                               const float *target_dev, float lr, float *loss_out);
 void mxp_cnn_destroy(mxp_cnn *net);
+/* One 3x3 convolution of the network's kind on the tensor cores (tcgen05,
+ * bfloat16 operands, float32 accumulation), the building block of the
+ * learned stage exposed on its own.  Zero padding 1; the logical input is
+ * Hl x Wl = Hs x Ws, or 2 Hs x 2 Ws nearest-upsampled when upsample = 1
+ * (stride 1 only); Ho = ceil(Hl / stride), Wo = ceil(Wl / stride).  Float32 NCHW
+ * device arrays, weights W [Cout][Cin][3][3] as bfloat16 bits.
+ *  mode 0 (forward):   out [N][Cout][Ho][Wo] = act(bias + conv(a)), a = the input
+ *                      [N][Cin][Hs][Ws] rounded to bfloat16, act = relu when
+ *                      relu != 0, bias nullable; Cout <= 64.
+ *  mode 1 (input gradient, upsample = 0): out [N][Cin][Hs][Ws] = the gradient
+ *                      of sum(g * conv(x)) w.r.t. x, a = g [N][Cout][Ho][Wo]
+ *                      rounded to bfloat16; Cin <= 64.
+ *  mode 2 (weight gradient): out [Cout][Cin * 9] = the gradient w.r.t. W, a = x
+ *                      [N][Cin][Hs][Ws], b = g [N][Cout][Ho][Wo], both rounded to
+ *                      bfloat16; Cout <= 64; out is overwritten.
+ * Work is ordered on cuda_stream, which the call synchronises once (to read the
+ * kernels' wait status: MXP_ETIMEOUT if a bounded wait gave up).  MXP_EINVAL
+ * for inconsistent sizes.  No counterpart in the paper. */
+mxp_status mxp_cnn_conv3x3(int mode, int stride, int upsample, int N, int Cin, int Hs, int Ws, int Cout,
+                           int Ho, int Wo, const float *a_dev, const float *b_dev, const void *w_bf16_dev,
+                           const float *bias_dev, int relu, float *out_dev, void *cuda_stream);
+
 /* Use net as the first preconditioner of every FGMRES iteration of prob (2D):
  * the direction z = net(v) is kept when the scaled residual
  * min_a ||v - a A z|| / ||v|| <= accept_tol, otherwise MatExPre(v) is used.

@@ -1,6 +1,9 @@
 // Learned preconditioning stage: a six-layer U-Net-style CNN with bfloat16
 // weights and float32 accumulation, with hand-written forward, backward and
-// Adam kernels (training and inference run on the GPU).  The paper has no
+// Adam kernels (training and inference run on the GPU).  The forward
+// convolutions, the input gradients and the weight gradients run on the tensor
+// cores (tcgen05, bfloat16 operands, float32 accumulation in tensor memory;
+// conv_tc.cu); the bias gradients and the elementwise steps on CUDA cores.  The paper has no
 // learned stage; this is the project's own extension, used as an extra
 // FGMRES stage with MatExPre as fallback (see engine.cu).
 //
@@ -35,180 +38,26 @@ static int64_t layer_woff(int l)
 }
 int64_t cnn_num_params() { return layer_woff(6); }
 
-// ---------------------------------------------------------------- forward
-// Block: 16 x 16 output pixels, COB output channels; input channels in chunks
-// of CIB staged in shared memory with the 3x3 halo (and the stride / upsample
-// index map applied while staging).
-constexpr int TS = 16, CIB = 8;
-
-template <int S, int UPS, int COB>
-__global__ void __launch_bounds__(TS *TS) k_conv_fwd(const float *__restrict__ in, int Cin, int Hs,
-                                                     int Ws, const __nv_bfloat16 *__restrict__ w,
-                                                     const float *__restrict__ bias, int Cout,
-                                                     int Ho, int Wo, int relu,
-                                                     const float *__restrict__ skip,
-                                                     float *__restrict__ out,
-                                                     float *__restrict__ out_skip)
-{
-    constexpr int PH = S * (TS - 1) + 3;
-    __shared__ float patch[CIB][PH][PH];
-    __shared__ float wsm[COB][CIB][9];
-    const int ngrp = (Cout + COB - 1) / COB;
-    const int n = blockIdx.z / ngrp, cog = blockIdx.z % ngrp;
-    const int oy0 = blockIdx.y * TS, ox0 = blockIdx.x * TS;
-    const int ty = threadIdx.x / TS, tx = threadIdx.x % TS;
-    const int Hl = UPS ? 2 * Hs : Hs, Wl = UPS ? 2 * Ws : Ws;   // logical input size
-    const int iy0 = S * oy0 - 1, ix0 = S * ox0 - 1;
-    float acc[COB];
-#pragma unroll
-    for (int c = 0; c < COB; ++c) acc[c] = 0.f;
-    for (int c0 = 0; c0 < Cin; c0 += CIB) {
-        for (int i = threadIdx.x; i < CIB * PH * PH; i += TS * TS) {
-            const int c = i / (PH * PH), r = (i / PH) % PH, q = i % PH;
-            const int ci = c0 + c, y = iy0 + r, x = ix0 + q;
-            float v = 0.f;
-            if (ci < Cin && y >= 0 && y < Hl && x >= 0 && x < Wl) {
-                const int ys = UPS ? (y >> 1) : y, xs = UPS ? (x >> 1) : x;
-                v = in[(((int64_t)n * Cin + ci) * Hs + ys) * Ws + xs];
-            }
-            patch[c][r][q] = v;
-        }
-        for (int i = threadIdx.x; i < COB * CIB * 9; i += TS * TS) {
-            const int co = cog * COB + i / (CIB * 9), ci = c0 + (i / 9) % CIB, k = i % 9;
-            float v = 0.f;
-            if (co < Cout && ci < Cin) v = __bfloat162float(w[((int64_t)co * Cin + ci) * 9 + k]);
-            wsm[i / (CIB * 9)][(i / 9) % CIB][k] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int c = 0; c < CIB; ++c) {
-            float pv[9];
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                for (int kx = 0; kx < 3; ++kx) pv[ky * 3 + kx] = patch[c][S * ty + ky][S * tx + kx];
-#pragma unroll
-            for (int o = 0; o < COB; ++o) {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) acc[o] = fmaf(wsm[o][c][k], pv[k], acc[o]);
-            }
-        }
-        __syncthreads();
-    }
-    const int oy = oy0 + ty, ox = ox0 + tx;
-    if (oy < Ho && ox < Wo) {
-#pragma unroll
-        for (int o = 0; o < COB; ++o) {
-            const int co = cog * COB + o;
-            if (co >= Cout) continue;
-            float v = acc[o] + bias[co];
-            if (relu) v = fmaxf(v, 0.f);
-            const int64_t q = (((int64_t)n * Cout + co) * Ho + oy) * Wo + ox;
-            out[q] = v;
-            if (out_skip) out_skip[q] = v + skip[q];
-        }
-    }
-}
-
 // ---------------------------------------------------------------- backward
-// gin[n, ci, y, x] (logical input, full resolution when UPS) =
-//   sum_{co, ky, kx} W[co, ci, ky, kx] gout[n, co, oy, ox],  S oy + ky - 1 = y.
-template <int S>
-__global__ void k_conv_bwd_data(const float *__restrict__ gout, int Cout, int Ho, int Wo,
-                                const __nv_bfloat16 *__restrict__ w, int Cin, int Hl, int Wl,
-                                float *__restrict__ gin)
+// gb[co] = sum over images and pixels of gout[n, co, :, :]; one block per
+// channel, fixed-order reduction.
+__global__ void __launch_bounds__(256) k_bias_grad(const float *__restrict__ gout, int N, int Cout, int64_t hw,
+                                                   float *__restrict__ gb)
 {
-    constexpr int CB = 8;
-    extern __shared__ float wsh[];           // [CB][Cout][9]
-    const int ngrp = (Cin + CB - 1) / CB;
-    const int n = blockIdx.z / ngrp, cg = blockIdx.z % ngrp;
-    for (int i = threadIdx.x; i < CB * Cout * 9; i += blockDim.x) {
-        const int c = i / (Cout * 9), co = (i / 9) % Cout, k = i % 9;
-        const int ci = cg * CB + c;
-        wsh[i] = (ci < Cin) ? __bfloat162float(w[((int64_t)co * Cin + ci) * 9 + k]) : 0.f;
+    const int co = blockIdx.x;
+    float acc = 0.f;
+    for (int n = 0; n < N; ++n) {
+        const float *g = gout + ((int64_t)n * Cout + co) * hw;
+        for (int64_t p = threadIdx.x; p < hw; p += blockDim.x) acc += g[p];
     }
+    __shared__ float red[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    const int x = blockIdx.x * 16 + threadIdx.x % 16, y = blockIdx.y * 16 + threadIdx.x / 16;
-    if (x >= Wl || y >= Hl) return;
-    float acc[CB];
-#pragma unroll
-    for (int c = 0; c < CB; ++c) acc[c] = 0.f;
-    for (int co = 0; co < Cout; ++co) {
-        const float *g = gout + ((int64_t)n * Cout + co) * Ho * Wo;
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky) {
-            const int t = y + 1 - ky;
-            if (t < 0 || (S == 2 && (t & 1))) continue;
-            const int oy = t / S;
-            if (oy >= Ho) continue;
-#pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
-                const int u = x + 1 - kx;
-                if (u < 0 || (S == 2 && (u & 1))) continue;
-                const int ox = u / S;
-                if (ox >= Wo) continue;
-                const float gv = g[(int64_t)oy * Wo + ox];
-#pragma unroll
-                for (int c = 0; c < CB; ++c) acc[c] = fmaf(wsh[(c * Cout + co) * 9 + ky * 3 + kx], gv, acc[c]);
-            }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < CB; ++c) {
-        const int ci = cg * CB + c;
-        if (ci < Cin) gin[(((int64_t)n * Cin + ci) * Hl + y) * Wl + x] = acc[c];
-    }
-}
-
-// gW[co, ci, k] = sum_{n, oy, ox} gout[n, co, oy, ox] xin[n, ci, S oy + ky - 1, S ox + kx - 1]
-// (xin logical: nearest-upsampled when UPS); gb[co] = sum gout (written by the ci = 0 block).
-// One block per (co, ci), fixed-order reduction.
-template <int S, int UPS>
-__global__ void __launch_bounds__(256) k_conv_bwd_weight(const float *__restrict__ xin, int N, int Cin,
-                                                         int Hs, int Ws,
-                                                         const float *__restrict__ gout, int Cout,
-                                                         int Ho, int Wo, float *__restrict__ gw,
-                                                         float *__restrict__ gb)
-{
-    const int co = blockIdx.x / Cin, ci = blockIdx.x % Cin;
-    const int Hl = UPS ? 2 * Hs : Hs, Wl = UPS ? 2 * Ws : Ws;
-    float acc[10];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) acc[k] = 0.f;
-    const int64_t npix = (int64_t)N * Ho * Wo;
-    for (int64_t p = threadIdx.x; p < npix; p += blockDim.x) {
-        const int n = (int)(p / ((int64_t)Ho * Wo));
-        const int r = (int)(p % ((int64_t)Ho * Wo));
-        const int oy = r / Wo, ox = r % Wo;
-        const float gv = gout[((int64_t)n * Cout + co) * Ho * Wo + r];
-        acc[9] += gv;
-        const float *xb = xin + ((int64_t)n * Cin + ci) * Hs * Ws;
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky) {
-            const int y = S * oy + ky - 1;
-            if (y < 0 || y >= Hl) continue;
-#pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
-                const int x = S * ox + kx - 1;
-                if (x < 0 || x >= Wl) continue;
-                const float xv = UPS ? xb[(int64_t)(y >> 1) * Ws + (x >> 1)] : xb[(int64_t)y * Ws + x];
-                acc[ky * 3 + kx] = fmaf(gv, xv, acc[ky * 3 + kx]);
-            }
-        }
-    }
-    __shared__ float red[8][10];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) {
-        float v = acc[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 10) {
+    if (threadIdx.x == 0) {
         float v = 0.f;
-        for (int i = 0; i < 8; ++i) v += red[i][threadIdx.x];
-        if (threadIdx.x < 9) gw[((int64_t)co * Cin + ci) * 9 + threadIdx.x] = v;
-        else if (ci == 0) gb[co] = v;
+        for (int i = 0; i < 8; ++i) v += red[i];
+        gb[co] = v;
     }
 }
 
@@ -330,6 +179,7 @@ struct mxp_cnn {
     float *x = nullptr, *a[6] = {nullptr}, *r5 = nullptr, *y = nullptr;
     float *gy = nullptr, *g5 = nullptr, *gfull = nullptr, *gh = nullptr, *gh2 = nullptr, *g1 = nullptr;
     double *partial = nullptr;
+    unsigned *err = nullptr;       // set by a tensor-core convolution whose bounded wait gave up
     float *loss_dev = nullptr;
     float *loss_host = nullptr;
     int adam_t = 0;
@@ -356,17 +206,8 @@ void conv_fwd(const mxp_cnn *net, int l, const float *in, int N, int Hs, int Ws,
     const CnnLayer L = kNet[l];
     const __nv_bfloat16 *w = net->wb + layer_woff(l);
     const float *b = net->w + layer_woff(l) + (int64_t)L.cin * L.cout * 9;
-    dim3 grid((Wo + TS - 1) / TS, (Ho + TS - 1) / TS);
-    count_launch();
-    if (L.cout >= 16) {
-        grid.z = N * ((L.cout + 15) / 16);
-        k_conv_fwd<S, UPS, 16><<<grid, TS * TS, 0, net->stream>>>(in, L.cin, Hs, Ws, w, b, L.cout, Ho, Wo,
-                                                                   L.relu, skip, out, out_skip);
-    } else {
-        grid.z = N * ((L.cout + 1) / 2);
-        k_conv_fwd<S, UPS, 2><<<grid, TS * TS, 0, net->stream>>>(in, L.cin, Hs, Ws, w, b, L.cout, Ho, Wo,
-                                                                  L.relu, skip, out, out_skip);
-    }
+    conv_fwd_tc(S, UPS, in, N, L.cin, Hs, Ws, w, b, L.cout, Ho, Wo, L.relu, skip, out, out_skip, net->err,
+                net->stream);
 }
 
 template <int S>
@@ -374,11 +215,8 @@ void conv_bwd_data(const mxp_cnn *net, int l, const float *gout, int N, int Ho, 
                    float *gin)
 {
     const CnnLayer L = kNet[l];
-    dim3 grid((Wl + 15) / 16, (Hl + 15) / 16, N * ((L.cin + 7) / 8));
-    const size_t smem = (size_t)8 * L.cout * 9 * sizeof(float);
-    count_launch();
-    k_conv_bwd_data<S><<<grid, 256, smem, net->stream>>>(gout, L.cout, Ho, Wo, net->wb + layer_woff(l),
-                                                         L.cin, Hl, Wl, gin);
+    conv_bwd_data_tc(S, gout, N, L.cout, Ho, Wo, net->wb + layer_woff(l), L.cin, Hl, Wl, gin, net->err,
+                     net->stream);
 }
 
 template <int S, int UPS>
@@ -388,9 +226,9 @@ void conv_bwd_weight(const mxp_cnn *net, int l, const float *xin, int N, int Hs,
     const CnnLayer L = kNet[l];
     float *gw = net->g + layer_woff(l);
     float *gb = gw + (int64_t)L.cin * L.cout * 9;
+    conv_wgrad_tc(S, UPS, xin, N, L.cin, Hs, Ws, gout, L.cout, Ho, Wo, gw, net->err, net->stream);
     count_launch();
-    k_conv_bwd_weight<S, UPS><<<L.cout * L.cin, 256, 0, net->stream>>>(xin, N, L.cin, Hs, Ws, gout, L.cout,
-                                                                       Ho, Wo, gw, gb);
+    k_bias_grad<<<L.cout, 256, 0, net->stream>>>(gout, N, L.cout, (int64_t)Ho * Wo, gb);
 }
 
 mxp_status check_shape(const mxp_cnn *net, int N, int H, int W)
@@ -496,12 +334,14 @@ mxp_status mxp_cnn_create(int device, void *cuda_stream, int max_batch, int max_
     A((void **)&net->gfull, full * 64 * 4); A((void **)&net->gh, half * 64 * 4);
     A((void **)&net->gh2, half * 64 * 4);
     A((void **)&net->partial, 2048 * sizeof(double)); A((void **)&net->loss_dev, sizeof(float));
+    A((void **)&net->err, sizeof(unsigned));
     ok = ok && cudaMallocHost((void **)&net->loss_host, sizeof(float)) == cudaSuccess;
     if (ok) {
         ok = cudaMemsetAsync(net->w, 0, net->np * 4, net->stream) == cudaSuccess &&
              cudaMemsetAsync(net->m, 0, net->np * 4, net->stream) == cudaSuccess &&
              cudaMemsetAsync(net->v, 0, net->np * 4, net->stream) == cudaSuccess &&
              cudaMemsetAsync(net->wb, 0, net->np * 2, net->stream) == cudaSuccess &&
+             cudaMemsetAsync(net->err, 0, sizeof(unsigned), net->stream) == cudaSuccess &&
              cudaStreamSynchronize(net->stream) == cudaSuccess;
     }
     cudaSetDevice(prev);
@@ -536,12 +376,27 @@ mxp_status mxp_cnn_get_params(const mxp_cnn *net, float *host_params)
     return MXP_OK;
 }
 
+// Reads (and clears) the tensor-core error word; one stream synchronisation.
+static mxp_status check_tc_error(mxp_cnn *net)
+{
+    unsigned e = 0;
+    CKC(cudaMemcpyAsync(&e, net->err, sizeof(unsigned), cudaMemcpyDeviceToHost, net->stream));
+    CKC(cudaStreamSynchronize(net->stream));
+    if (e) {
+        CKC(cudaMemsetAsync(net->err, 0, sizeof(unsigned), net->stream));
+        return cfail(MXP_ETIMEOUT, "a tensor-core convolution's bounded wait gave up");
+    }
+    return MXP_OK;
+}
+
 mxp_status mxp_cnn_forward(mxp_cnn *net, int N, int H, int W, const float *x_dev, float *y_dev)
 {
     if (!net || !x_dev || !y_dev) return cfail(MXP_EINVAL, "NULL argument");
     mxp_status s = check_shape(net, N, H, W);
     if (s != MXP_OK) return s;
-    return forward_impl(net, N, H, W, x_dev, y_dev);
+    s = forward_impl(net, N, H, W, x_dev, y_dev);
+    if (s != MXP_OK) return s;
+    return check_tc_error(net);
 }
 
 mxp_status mxp_cnn_backward(mxp_cnn *net, const float *x_dev, const float *gy_dev, float *grad_dev)
@@ -579,7 +434,8 @@ mxp_status mxp_cnn_train_step(mxp_cnn *net, int N, int H, int W, const float *x_
     CKC(cudaGetLastError());
     if (loss_out) {
         CKC(cudaMemcpyAsync(net->loss_host, net->loss_dev, sizeof(float), cudaMemcpyDeviceToHost, net->stream));
-        CKC(cudaStreamSynchronize(net->stream));
+        s = check_tc_error(net);
+        if (s != MXP_OK) return s;
         *loss_out = *net->loss_host;
         if (!std::isfinite(*loss_out)) return cfail(MXP_ENAN, "training loss is not finite");
     }
@@ -595,6 +451,7 @@ void mxp_cnn_destroy(mxp_cnn *net)
                      net->loss_dev};
     for (float *b : bufs) cudaFree(b);
     cudaFree(net->wb);
+    cudaFree(net->err);
     cudaFree(net->partial);
     if (net->loss_host) cudaFreeHost(net->loss_host);
     delete net;
@@ -618,5 +475,5 @@ mxp_status mxp::cnn_apply_vector(mxp_cnn *net, int n0, int n1, const double2 *v,
     count_launch();
     k_unpack_output<<<ew_grid(n), 256, 0, net->stream>>>(net->y, n, z);
     CKC(cudaGetLastError());
-    return MXP_OK;
+    return check_tc_error(net);
 }

@@ -120,6 +120,49 @@ def evaluate(net, n_interior=1024, npml=32, seeds=(0,), accept_tol=0.5,
     return rows
 
 
+def _rho(G, v, z):
+    """Acceptance ratio of a direction: min_a ||v - a A z|| / ||v||."""
+    import torch
+    az = G.apply_operator(z)
+    vv = float(torch.vdot(v, v).real)
+    aa = float(torch.vdot(az, az).real)
+    va = torch.vdot(az, v)
+    if aa <= 0 or vv <= 0:
+        return 1.0
+    return float(max(0.0, 1.0 - abs(complex(va)) ** 2 / (aa * vv)) ** 0.5)
+
+
+def direction_study(net, n_interior=1024, npml=32, seed=0, iterates=5, seed_base=I.SEED_BASE + 6000):
+    """The acceptance ratio rho = min_a ||v - a A z|| / ||v|| of MatExPre's
+    direction z = MatExPre(v) and of the network's z = net(v), for the first
+    FGMRES residual directions v of a held-out problem.  A learned direction is
+    kept when rho <= accept_tol; this tells which thresholds MatExPre's own
+    directions would pass."""
+    import torch
+    g, c, p, G = _problem(n_interior, npml, seed_base + seed)
+    b = torch.from_numpy(I.rhs_from_source(I.gaussian_source(g)).ravel()).cuda()
+    ny, nx = g.shape
+    cmax = float(c.max())
+    cf = torch.from_numpy((c / cmax).astype(np.float32).reshape(ny, nx)).cuda()
+    rows = []
+    for k in range(iterates):
+        if k == 0:
+            r = b.clone()
+        else:
+            x, _ = G.solve(b, rtol=1e-12, maxit=k, check=False)
+            r = b - G.apply_operator(x)
+        v = r / torch.linalg.vector_norm(r)
+        zm, st = G.apply_matexpre(v)
+        vs = v * (v.numel() ** 0.5)                    # unit root-mean-square, as the stage feeds the network
+        xin = torch.stack([vs.real.reshape(ny, nx).float(), vs.imag.reshape(ny, nx).float(), cf])[None]
+        y = net.forward(xin.contiguous())
+        zn = torch.complex(y[0, 0].double(), y[0, 1].double()).reshape(-1).contiguous()
+        rows.append(dict(iterate=k, rho_matexpre=_rho(G, v, zm), rho_network=_rho(G, v, zn),
+                         matexpre_inner=st["inner_iters"]))
+    G.close()
+    return rows
+
+
 def main():
     import argparse
     import torch
@@ -130,24 +173,30 @@ def main():
     ap.add_argument("--iterates", type=int, default=5)
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--eval-size", type=int, default=1024)
-    ap.add_argument("--accept-tol", type=float, default=0.5)
+    ap.add_argument("--accept-tol", type=float, nargs="+", default=[0.5])
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default="learned_stage")
     a = ap.parse_args()
     t0 = time.time()
     X, T = generate_pairs(a.train_size, 16, tuple(range(a.media)), a.sources, a.iterates)
     t_gen = time.time() - t0
-    net = N.Cnn(32, CROP, CROP)                       # training instance (batches of crops)
+    print(json.dumps(dict(stage="pairs", crops=int(len(X)), gen_s=t_gen)), flush=True)
+    net = N.Cnn(a.batch, CROP, CROP)                  # training instance (batches of crops)
     net.set_params(I.cnn_initial_params(I.SEED_BASE + 7000))
     t0 = time.time()
-    hist = train(net, X, T, epochs=a.epochs)
+    hist = train(net, X, T, epochs=a.epochs, batch=a.batch, lr=a.lr)
     torch.cuda.synchronize()
     t_train = time.time() - t0
+    print(json.dumps(dict(stage="train", epochs=len(hist), train_s=t_train, loss=hist)), flush=True)
     save(net, a.out, dict(crops=int(len(X)), epochs=len(hist), loss=hist))
     side = a.eval_size + 64
     inf = N.Cnn(1, side, side)                         # inference instance (one full grid)
     inf.set_params(net.get_params())
-    rows = evaluate(inf, a.eval_size, 32, (0,), a.accept_tol)
-    print(json.dumps(dict(crops=int(len(X)), gen_s=t_gen, train_s=t_train, loss=hist, eval=rows)))
+    print(json.dumps(dict(stage="directions", rows=direction_study(inf, a.eval_size, 32))), flush=True)
+    for tol in a.accept_tol:
+        rows = evaluate(inf, a.eval_size, 32, (0,), tol)
+        print(json.dumps(dict(stage="eval", accept_tol=tol, crops=int(len(X)), eval=rows)), flush=True)
 
 
 if __name__ == "__main__":

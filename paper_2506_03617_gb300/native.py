@@ -104,6 +104,7 @@ SIGNATURES = {
                                       ct.c_void_p, ct.c_float, ct.POINTER(ct.c_float)]),
     "mxp_cnn_destroy": (None, [ct.c_void_p]),
     "mxp_attach_cnn": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_double]),
+    "mxp_cnn_conv3x3": (ct.c_int, [ct.c_int] * 10 + [ct.c_void_p] * 4 + [ct.c_int, ct.c_void_p, ct.c_void_p]),
     "mxp_selftest_barrier_timeout": (ct.c_int, [ct.c_void_p]),
     "mxp_kernel_launch_count": (ct.c_int64, []),
     "mxp_num_tile_configs": (ct.c_int, []),
@@ -379,6 +380,34 @@ class Cnn:
         _check(self._lib.mxp_cnn_train_step(self._h, n, h, w, self._fptr(x), self._fptr(target),
                                             float(lr), ct.byref(loss)))
         return float(loss.value)
+
+
+def conv3x3(mode, a, w_bf16=None, b=None, bias=None, stride=1, upsample=False, relu=False, cout=None,
+            in_hw=None):
+    """One tensor-core 3x3 convolution (mxp_cnn_conv3x3).  a: float32 CUDA tensor
+    [N, C, H, W] (mode 0, 2: the input x; mode 1: the output gradient g);
+    w_bf16: torch.bfloat16 CUDA tensor [Cout, Cin, 3, 3] (modes 0, 1); b: the
+    output gradient g (mode 2); cout: output channels (mode 2 only); in_hw: the
+    input's (H, W) for mode 1 (default: the gradient's size times the stride)."""
+    import torch
+    N = int(a.shape[0])
+    if mode == 1:
+        Cout, Ho, Wo = int(a.shape[1]), int(a.shape[2]), int(a.shape[3])
+        Cin = int(w_bf16.shape[1])
+        Hs, Ws = (int(in_hw[0]), int(in_hw[1])) if in_hw else (Ho * stride, Wo * stride)
+        out = torch.empty((N, Cin, Hs, Ws), dtype=torch.float32, device=a.device)
+    else:
+        Cin, Hs, Ws = int(a.shape[1]), int(a.shape[2]), int(a.shape[3])
+        Hl, Wl = (2 * Hs, 2 * Ws) if upsample else (Hs, Ws)
+        Ho, Wo = (Hl + stride - 1) // stride, (Wl + stride - 1) // stride
+        Cout = int(w_bf16.shape[0]) if mode == 0 else int(cout)
+        out = (torch.empty((N, Cout, Ho, Wo), dtype=torch.float32, device=a.device) if mode == 0
+               else torch.empty((Cout, Cin * 9), dtype=torch.float32, device=a.device))
+    ptr = lambda t: ct.c_void_p(t.data_ptr()) if t is not None else None
+    _check(load().mxp_cnn_conv3x3(int(mode), int(stride), int(bool(upsample)), N, Cin, Hs, Ws, Cout, Ho, Wo,
+                                  ptr(a), ptr(b), ptr(w_bf16), ptr(bias), int(bool(relu)), ptr(out),
+                                  _stream_handle(None)))
+    return out
 
 
 def attach_cnn(problem, net, accept_tol=0.5):

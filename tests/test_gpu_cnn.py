@@ -1,6 +1,10 @@
-"""Learned stage on the GPU: forward and backward kernels against the fp64 CNN
-oracle (same bfloat16-rounded weights), training reduces the loss, and the
-learned FGMRES stage keeps the solve correct with MatExPre as fallback."""
+"""Learned stage on the GPU: the tensor-core (tcgen05) forward convolutions and
+input gradients and the weight-gradient kernels against the fp64 CNN oracle
+(same bfloat16-rounded weights; the oracle rounds every tensor-core operand to
+bfloat16 as the kernels do: the convolution inputs in the forward pass and
+the incoming gradients of the input gradients), training reduces the loss,
+and the learned FGMRES stage keeps the solve correct with MatExPre as
+fallback."""
 import numpy as np
 import pytest
 
@@ -37,6 +41,16 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def _log(what, a, b):
+    """Measured errors behind the bounds (appended to MXP_PARITY_LOG when set)."""
+    import json
+    import os
+    path = os.environ.get("MXP_PARITY_LOG")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps({"what": what, "l2_or_weight": float(a), "max_or_bias": float(b)}) + "\n")
+
+
 def test_forward_and_backward_match_the_oracle(native):
     rng = np.random.default_rng(1)
     theta = I.cnn_initial_params(3) + (0.02 * rng.standard_normal(C.num_params())).astype(np.float32)
@@ -47,17 +61,28 @@ def test_forward_and_backward_match_the_oracle(native):
     xd = torch.from_numpy(x).cuda()
     y = net.forward(xd).cpu().numpy()
     th = _bf16(theta)
-    y_ref, cache = C.forward(th, x.astype(np.float64))
-    assert _rel(y, y_ref) < 1e-5
+    y_ref, cache = C.forward(th, x.astype(np.float64), round_operands=True)
+    # Same bfloat16 operands on both sides, but a float32 activation and its
+    # float64 counterpart now and then round to different bfloat16 neighbours;
+    # each such flip perturbs the next layer's sums enough to cause more flips, so
+    # over six layers the network outputs differ by far more than float32
+    # accumulation (each convolution alone agrees within 1e-5: test_gpu_conv_tc).
+    # Measured on GB300: 4.8e-4 (l2), 2.1e-3 (max).
+    e_fwd = (_rel(y, y_ref), np.max(np.abs(y - y_ref)) / np.max(np.abs(y_ref)))
+    _log("cnn forward", *e_fwd)
+    assert e_fwd[0] < 2e-3 and e_fwd[1] < 1e-2, e_fwd
     gy = rng.standard_normal(y.shape).astype(np.float32)
     g = net.backward(xd, torch.from_numpy(gy).cuda()).cpu().numpy()
-    g_ref, _ = C.backward(th, cache, gy.astype(np.float64))
+    g_ref, _ = C.backward(th, cache, gy.astype(np.float64), round_operands=True)
     # per layer (weights and biases separately)
     k = 0
-    for ci, co, _, _, _ in C.LAYERS:
+    for li, (ci, co, _, _, _) in enumerate(C.LAYERS):
         nw = ci * co * 9
-        assert _rel(g[k:k + nw], g_ref[k:k + nw]) < 1e-4
-        assert _rel(g[k + nw:k + nw + co], g_ref[k + nw:k + nw + co]) < 1e-4
+        ew, eb = _rel(g[k:k + nw], g_ref[k:k + nw]), _rel(g[k + nw:k + nw + co], g_ref[k + nw:k + nw + co])
+        _log(f"cnn layer {li + 1} weight / bias gradient", ew, eb)
+        # the same flips run back through the five input gradients (measured on
+        # GB300: at most 1.3e-2 for a weight and 1.5e-2 for a bias gradient)
+        assert ew < 4e-2 and eb < 4e-2, (li, ew, eb)
         k += nw + co
 
 

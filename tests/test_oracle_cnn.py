@@ -66,3 +66,33 @@ def test_network_gradients_match_central_differences():
 def test_parameter_count_and_layer_list_agree_with_the_input_module():
     assert C.num_params() == I.cnn_initial_params(0).size
     assert [tuple(l) for l in C.LAYERS] == [tuple(l) for l in I.CNN_LAYERS]
+
+
+def test_bf16_rounding_matches_torch_and_ties_to_even():
+    """The oracle's bfloat16 operand rounding equals torch's float32 -> bfloat16
+    conversion (round to nearest, ties to even) on random values, and resolves
+    the exact halfway cases to the even neighbour."""
+    import torch
+    rng = np.random.default_rng(9)
+    v = np.concatenate([rng.standard_normal(5000) * 10.0 ** rng.integers(-6, 6, 5000),
+                        [0.0, -0.0, 1.0, -3.5]])
+    ref = torch.from_numpy(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(C.round_bf16(v), ref)
+    one = np.float32(1.0).view(np.uint32)
+    half_up = np.array([one + 0x8000], dtype=np.uint32).view(np.float32)     # 1 + 2^-8: tie, even is 1
+    half_up2 = np.array([one + 0x18000], dtype=np.uint32).view(np.float32)   # tie whose even neighbour is above
+    assert C.round_bf16(half_up)[0] == 1.0
+    assert C.round_bf16(half_up2)[0] == np.array([one + 0x20000], dtype=np.uint32).view(np.float32)[0]
+
+
+def test_rounded_operands_change_the_output_by_bf16_rounding_only():
+    rng = np.random.default_rng(10)
+    theta = rng.standard_normal(C.num_params()) * 0.1
+    x = rng.standard_normal((1, 3, 8, 8))
+    y, _ = C.forward(theta, x)
+    yq, cache = C.forward(theta, x, round_operands=True)
+    rel = np.linalg.norm(y - yq) / np.linalg.norm(y)
+    assert 0 < rel < 2e-2
+    _, c0 = C.forward(theta, x)
+    for k in c0:                                      # cached activations differ only through the rounding
+        assert c0[k].shape == cache[k].shape
