@@ -68,26 +68,37 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", choices=["c64", "bf16s", "c128"], default="c64")
+    ap.add_argument("--exp-tol", type=float, default=1e-3,
+                    help="truncation bound of the Taylor plan of every exp / psi_1 action (all "
+                         "precisions, the FP64 comparison included)")
+    ap.add_argument("--theta", type=float, default=6.0,
+                    help="largest sub-step norm of the Taylor plan (all precisions)")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-only", action="store_true",
                     help="timed solves only (no e2e, roofline, 3D, fp64 or CPU legs)")
-    ap.add_argument("--profile-case", choices=["2d", "3d"], default=None,
-                    help="run two exp actions of the 2D (1088^2) or 3D (288^3) workload "
-                         "and exit; a small command for ncu captures")
+    ap.add_argument("--profile-case", choices=["2d", "3d", "cnn"], default=None,
+                    help="run two exp actions of the 2D (1088^2) or 3D (288^3) workload with the "
+                         "benchmark's Taylor plan, or two training steps of the learned stage's "
+                         "network on 32 crops of 64 x 64 (cnn), and exit; a small command for ncu")
     ap.add_argument("--record-traffic", nargs=3, metavar=("KERNEL", "PREC", "NCU_CSV"), default=None,
                     help="parse an ncu --csv --print-units base log of dram__bytes_read/write.sum "
                          "for KERNEL (persist2d, fused2d or horner_step) and store the DRAM bytes per "
                          "launch with the kernel source hash in profiles/traffic.json; then exit")
     ap.add_argument("--experiment", choices=["precond", "marmousi", "fused3d", "solve3d", "c3",
-                                             "precision", "oracle"], default=None,
+                                             "precision", "oracle", "c4", "plan"], default=None,
                     help="run one of the side measurements (one JSON line per case) and exit: "
                          "precond = Algorithm 1 vs P_N vs the psi_2 variant on the 1088^2 "
                          "workload; marmousi = mixed boundary conditions on a Marmousi-shaped "
                          "grid vs a PML grid of the same size; fused3d = 3D sweep kernels; "
                          "c3 = 288^3 solves in FP64, complex64 and bf16 storage; precision = "
                          "errors of the low-precision solves against the FP64 oracle (c1) and "
-                         "the FP64 GPU path (c2); oracle = timed oracle runs on the host cores")
+                         "the FP64 GPU path (c2); oracle = timed oracle runs on the host cores; "
+                         "c4 = the multi-source batch (64 sources on 8 mixed 2D media in one grouped "
+                         "call, then 8 sources on 432^3 in waves); plan = Taylor plans (exp_tol, "
+                         "theta_max) on the 1088^2 workload: sweeps, action errors, solve time")
+    ap.add_argument("--c4-3d-waves", type=int, default=2,
+                    help="with --experiment c4: waves of the 8 3D sources (0 skips the 3D part)")
     ap.add_argument("--persist-cfg", type=int, default=None,
                     help="with --profile-case 2d: force this persistent-kernel configuration "
                          "(skips the autotuner's other candidates)")
@@ -106,13 +117,14 @@ def workload():
     return grid, c, p, b
 
 
-def config_dict(grid, prec, rtol):
+def config_dict(grid, prec, rtol, exp_tol=None, theta=None):
+    plan = "" if exp_tol is None else f", Taylor plan exp_tol {exp_tol:g} theta_max {theta:g}"
     return {"workload": "2d_layered_1088",
             "grid": f"{grid.ni[0]}x{grid.ni[1]} interior + {grid.npml}-cell PML = "
                     f"{grid.n[0]}x{grid.n[1]} unknowns",
             "medium": "layered 1.5-4.5 x (1 + 0.15 GRF, corr. 20 cells), seeded",
             "source": "Gaussian sigma=h at centre", "ppw": 8,
-            "method": f"FGMRES(30) fp64, MatExPre apply in {prec}, fprtol 0.08, t=40h^2, s=1/freq",
+            "method": f"FGMRES(30) fp64, MatExPre apply in {prec}, fprtol 0.08, t=40h^2, s=1/freq{plan}",
             "rtol": rtol, "l2": "flushed (256 MiB write) before every timed step",
             "parallelism": "medium replicated, sources split across GPUs (one source per GPU: "
                            "the centre source on rank 0, seeded positions on the others; weak scaling)"}
@@ -319,7 +331,8 @@ def run_ours(args):
     mine = D.shard(range(len(sources)), rank, world)
     b_host = sources[mine[0]]
     prob = N.Problem.from_grid(grid, c, p, device=dev)
-    prob.set_params(prec=args.prec, exp_tol=1e-12 if args.prec == "c128" else 1e-6)
+    plan = dict(exp_tol=args.exp_tol, theta_max=args.theta)
+    prob.set_params(prec=args.prec, **plan)
     stream = prob.stream
     b = torch.from_numpy(b_host).to(f"cuda:{dev}")
     x = prob.empty()
@@ -452,7 +465,7 @@ def run_ours(args):
         g3, c3, p3 = I.config_3d_homogeneous()
         del flush
         P3 = N.Problem.from_grid(g3, c3, p3, device=dev)
-        P3.set_params(prec=args.prec, exp_tol=1e-12 if args.prec == "c128" else 1e-6)
+        P3.set_params(prec=args.prec, **plan)
         x3 = torch.ones(g3.n_total, dtype=torch.complex128, device=f"cuda:{dev}")
         y3 = P3.empty()
         with torch.cuda.stream(P3.stream):
@@ -499,7 +512,7 @@ def run_ours(args):
         cb_ = I.layered_grf(gb_, I.SEED_BASE + 3000 + 512)
         pb_ = I.paper_params(gb_, cb_, ppw=8.0)
         PB = N.Problem.from_grid(gb_, cb_, pb_, device=dev)
-        PB.set_params(prec=args.prec, exp_tol=1e-12 if args.prec == "c128" else 1e-6)
+        PB.set_params(prec=args.prec, **plan)
         bsrc = [torch.from_numpy(I.rhs_from_source(I.gaussian_source(gb_, center=ctr)).ravel())
                 .to(f"cuda:{dev}") for ctr in I.random_centers(gb_, 8, seed=I.SEED_BASE + 3612)]
         xsb = [PB.empty() for _ in bsrc]
@@ -526,7 +539,7 @@ def run_ours(args):
             # the plain FP64 path on the same problem, and the other low-precision
             # storage; errors of the low-precision solutions against the FP64 one
             x_lo = x.clone()
-            prob.set_params(prec="c128", exp_tol=1e-12)
+            prob.set_params(prec="c128", **plan)
             x64 = prob.empty()
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -551,7 +564,7 @@ def run_ours(args):
                                    f"{args.prec}_solution_rel_err":
                                        float(torch.linalg.vector_norm(x_lo - x64)) / nrm64}
             other = "bf16s" if args.prec == "c64" else "c64"
-            prob.set_params(prec=other, exp_tol=1e-6)
+            prob.set_params(prec=other, **plan)
             xo = prob.empty()
             prob.solve(b, xo, rtol=rtol, maxit=300)                # tuning and first launches
             torch.cuda.synchronize()
@@ -568,7 +581,7 @@ def run_ours(args):
                                        "solution_rel_err_vs_fp64":
                                            float(torch.linalg.vector_norm(xo - x64)) / nrm64}
             del x64, xo, x_lo
-            prob.set_params(prec=args.prec, exp_tol=1e-6)
+            prob.set_params(prec=args.prec, **plan)
 
     cpu = None
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
@@ -586,7 +599,7 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
-                "data": "synthetic", "config": config_dict(grid, args.prec, rtol),
+                "data": "synthetic", "config": config_dict(grid, args.prec, rtol, args.exp_tol, args.theta),
                 "time_to_1e-6_s": total_max / args.steps,
                 "solve": {"outer": st0["outer_iters"], "inner_total": st0["inner_iters_total"],
                           "true_relres": max(s["true_relres"] for s in stats),
@@ -606,13 +619,24 @@ def run_profile_case(args):
     import torch
     from paper_2506_03617_gb300 import inputs as I
     from paper_2506_03617_gb300 import native as N
+    if args.profile_case == "cnn":
+        import numpy as np
+        rng = np.random.default_rng(0)
+        net = N.Cnn(32, 64, 64)
+        net.set_params(I.cnn_initial_params(I.SEED_BASE + 7000))
+        x = torch.from_numpy(rng.standard_normal((32, 3, 64, 64)).astype(np.float32)).cuda()
+        t = torch.from_numpy(rng.standard_normal((32, 2, 64, 64)).astype(np.float32)).cuda()
+        losses = [net.train_step(x, t, 1e-3) for _ in range(2)]
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "cnn", "batch": 32, "size": 64, "loss": losses}))
+        return 0
     if args.profile_case == "3d":
         g, c, p = I.config_3d_homogeneous()
     else:
         g, c, p, _ = workload()
     prob = N.Problem.from_grid(g, c, p)
     kw = {} if args.persist_cfg is None else {"persist_cfg": args.persist_cfg}
-    prob.set_params(prec=args.prec, exp_tol=1e-12 if args.prec == "c128" else 1e-6, **kw)
+    prob.set_params(prec=args.prec, exp_tol=args.exp_tol, theta_max=args.theta, **kw)
     x = torch.ones(g.n_total, dtype=torch.complex128, device="cuda")
     y = prob.empty()
     for _ in range(2):
@@ -691,7 +715,7 @@ def run_experiment(args):
             prob = N.Problem.from_grid(g, c, p)
             sols = {}
             for pr in ("c64", "bf16s", "c128"):
-                prob.set_params(prec=pr, exp_tol=1e-12 if pr == "c128" else 1e-6)
+                prob.set_params(prec=pr, exp_tol=args.exp_tol, theta_max=args.theta)
                 if pr != "c128":
                     _timed_solve(prob, b, maxit=2)
                 x = prob.empty()
@@ -779,6 +803,96 @@ def run_experiment(args):
             print(json.dumps({"experiment": "oracle", "case": "c2 exp action at t/16", "threads": threads,
                               "seconds": secs, "gpts": pts / secs / 1e9}), flush=True)
         oracle.set_threads(ncores)
+    elif args.experiment == "c4":
+        # 2D: 64 sources on 8 media (3 x 288^2, 3 x 544^2, 2 x 1088^2 unknowns) in
+        # one mxp_solve_batch call: one group, every pass one launch over all of them
+        media = I.config_batched_2d()
+        probs, pofr, bs, xs, meta = [], [], [], [], []
+        for k, (g, c, p, centres) in enumerate(media):
+            G = N.Problem.from_grid(g, c, p)
+            G.set_params(prec=prec, exp_tol=args.exp_tol, theta_max=args.theta)
+            probs.append(G)
+            for j, ctr in enumerate(centres):
+                bs.append(torch.from_numpy(I.rhs_from_source(I.gaussian_source(g, center=ctr)).ravel()).cuda())
+                xs.append(G.empty())
+                pofr.append(k)
+                meta.append((k, j, list(g.n)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = N.solve_batch(probs, pofr, bs, xs, rtol=1e-6, maxit=300)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        for (k, j, n), q in zip(meta, st):
+            print(json.dumps({"experiment": "c4", "part": "2d", "medium": k, "source": j, "unknowns": n,
+                              "outer": q["outer_iters"], "inner": q["inner_iters_total"],
+                              "true_relres": q["true_relres"], "converged": q["converged"],
+                              "time_to_1e-6_s": q["seconds"]}), flush=True)
+        pts = sum(q["pt_updates"] for q in st)
+        print(json.dumps({"experiment": "c4", "part": "2d summary", "prec": prec, "sources": len(st),
+                          "wall_s": wall, "pt_updates": pts, "gpts": pts / wall / 1e9,
+                          "all_converged": all(q["converged"] for q in st),
+                          "max_true_relres": max(q["true_relres"] for q in st),
+                          "max_time_to_1e-6_s": max(q["seconds"] for q in st)}), flush=True)
+        del probs, bs, xs
+        torch.cuda.empty_cache()
+        if args.c4_3d_waves > 0:
+            # 3D: 8 sources on a 432^3 layered medium, batched in waves that fit
+            # HBM, FGMRES restart 8 and inner restart 8
+            g, c, p, centres = I.config_batched_3d()
+            G = N.Problem.from_grid(g, c, p)
+            G.set_params(prec=prec, exp_tol=args.exp_tol, theta_max=args.theta, inner_restart=8)
+            per = (len(centres) + args.c4_3d_waves - 1) // args.c4_3d_waves
+            t0 = time.perf_counter()
+            pts = 0
+            rows = []
+            for w0 in range(0, len(centres), per):
+                wave = centres[w0:w0 + per]
+                bw = [torch.from_numpy(I.rhs_from_source(I.gaussian_source(g, center=ctr)).ravel()).cuda()
+                      for ctr in wave]
+                xw = [G.empty() for _ in wave]
+                tw = time.perf_counter()
+                stw = N.solve_batch([G], [0] * len(wave), bw, xw, rtol=1e-6, restart=8, maxit=300)
+                torch.cuda.synchronize()
+                for j, q in enumerate(stw):
+                    rows.append(q)
+                    pts += q["pt_updates"]
+                    print(json.dumps({"experiment": "c4", "part": "3d", "source": w0 + j, "unknowns": list(g.n),
+                                      "wave": w0 // per, "outer": q["outer_iters"],
+                                      "inner": q["inner_iters_total"], "true_relres": q["true_relres"],
+                                      "converged": q["converged"],
+                                      "wave_time_s": time.perf_counter() - tw}), flush=True)
+                del bw, xw
+                torch.cuda.empty_cache()
+            wall = time.perf_counter() - t0
+            print(json.dumps({"experiment": "c4", "part": "3d summary", "prec": prec, "sources": len(rows),
+                              "waves": args.c4_3d_waves, "wall_s": wall, "pt_updates": pts,
+                              "gpts": pts / wall / 1e9, "all_converged": all(q["converged"] for q in rows),
+                              "max_true_relres": max(q["true_relres"] for q in rows)}), flush=True)
+    elif args.experiment == "plan":
+        # Taylor plans of the low-precision actions on the 1088^2 workload: sweeps
+        # per exp action, the action's error against the FP64 action (exp_tol
+        # 1e-12), and the time and iteration counts of the solve to 1e-6
+        grid, c, p, bh = workload()
+        b = torch.from_numpy(bh).cuda()
+        prob = N.Problem.from_grid(grid, c, p)
+        xv = torch.from_numpy(I.random_complex(grid.n_total, 5)).cuda()
+        prob.set_params(prec="c128", exp_tol=1e-12)
+        e128, s128 = prob.apply_phi(0, xv)[0], prob.apply_phi(1, xv)[0]
+
+        def rel(a, r):
+            return float(torch.linalg.vector_norm(a - r) / torch.linalg.vector_norm(r))
+
+        for tol, th in [(1e-6, 4), (1e-5, 6), (1e-4, 6), (1e-3, 6), (1e-3, 8), (1e-4, 10)]:
+            prob.set_params(prec=prec, exp_tol=tol, theta_max=th)
+            e, ps = prob.apply_phi(0, xv)
+            s1 = prob.apply_phi(1, xv)[0]
+            _timed_solve(prob, b, maxit=2)
+            row = _timed_solve(prob, b, maxit=400)
+            print(json.dumps({"experiment": "plan", "workload": "2d_layered_1088", "prec": prec,
+                              "exp_tol": tol, "theta_max": th, "sweeps_per_exp_action": ps,
+                              "exp_err_l2": rel(e, e128),
+                              "exp_err_max": float((e - e128).abs().max() / e128.abs().max()),
+                              "psi1_err_l2": rel(s1, s128), **row}), flush=True)
     elif args.experiment == "solve3d":
         # converging-lens medium of Sec. 4 on 128^3 + 16 PML, point-like source at the centre
         g, c, p = I.config_3d_lens(n_interior=128, npml=16)
