@@ -154,6 +154,39 @@ typedef struct mxp_problem mxp_problem;   /* opaque, library-owned */
 mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device,
                       void *cuda_stream, mxp_problem **out);
 
+/* Create a problem on a slab of a larger grid: rows [row0, row0 + nrows) of the
+ * last axis of `grid` (the y rows in 2D, the z planes in 3D), for a slab
+ * decomposition of one grid over several GPUs (the MPI / DMDA scheme of Sec. 4
+ * with one slab per rank and halo rows exchanged between ranks).  c_slab_host
+ * holds the wave speed of those rows (x fastest); c_range = {min, max} of c over
+ * the whole grid.  The PML coefficients follow the rows' global positions and
+ * the shift and Taylor plan are those of the whole grid (every slab of a grid
+ * gets the same mu, S and m), so that steps on overlapping slabs agree.  Beyond
+ * the slab's first and last rows the operator sees zero values: a caller keeps
+ * the rows it owns exact by running K steps on its rows plus K halo rows on each
+ * side, then exchanging halos.  Slabs run through mxp_horner_step and
+ * mxp_apply_operator (complex128); the whole-grid entry points (actions,
+ * MatExPre, solves, boundary faces, the learned stage) return MXP_EINVAL for a
+ * slab.  MXP_EINVAL also for rows outside the grid or a range that does not
+ * contain the slab's speeds. */
+mxp_status mxp_create_slab(const mxp_grid *grid, int64_t row0, int64_t nrows, const double *c_slab_host,
+                           const double *c_range, int device, void *cuda_stream, mxp_problem **out);
+
+/* One Taylor-Horner step of the exp / psi actions (Def. psi, Horner form of the
+ * sub-stepped Taylor polynomial), complex128:
+ *   out = rho (y + sigma (A_s - mu I) p + gamma v),
+ * with the problem's shift mu (mxp_get_plan) and complex scalars sigma, gamma,
+ * rho given as {re, im}; y and v nullable (v needs gamma).  One launch on the
+ * problem's stream; out must not alias p, y or v. */
+mxp_status mxp_horner_step(mxp_problem *prob, const double *sigma, const double *gamma, const double *rho,
+                           const void *p_dev, const void *y_dev, const void *v_dev, void *out_dev);
+
+/* The shift mu and the Taylor plan (S sub-steps of degree m) of action `which`
+ * (0 exp, 1 psi_1, 2 psi_2) for the current parameters: exp(i t A_s) v =
+ * e^{i t mu} (prod over S sub-steps of the degree-m Taylor polynomial of
+ * i t (A_s - mu) / S) v. */
+mxp_status mxp_get_plan(const mxp_problem *prob, int which, double *mu, int *S, int *m);
+
 /* Fill *p with the paper's rules for a grid whose slowest speed is c_min and
  * `ppw` points per slowest wavelength: omega = 2 pi c_min / (ppw h),
  * freq = 1/(ppw h), s = 1/freq, t = 40 h^2 (0.4/freq^2 at ppw 10), C_pml 20,

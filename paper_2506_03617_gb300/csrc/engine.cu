@@ -85,6 +85,11 @@ struct mxp_problem {
     Geom geom{};
     int64_t ntot = 0;
     double cmin = 0, cmax = 0;
+    // slab of a larger grid (mxp_create_slab): the problem holds rows
+    // [row0, row0 + geom.n[dim-1]) of the last axis of `grid`; coefficients and
+    // the Taylor plan follow the global grid, cmin / cmax are the global range
+    int slab = 0;
+    int64_t row0 = 0;
     mxp_params prm{};
     // device data
     double *c_dev = nullptr;
@@ -173,8 +178,9 @@ static void build_coef_host(mxp_problem *P)
     const double h = P->grid.h, ih2 = 1.0 / (h * h);
     P->coef_host.assign((size_t)9 * nm, make_double2(0, 0));
     for (int d = 0; d < P->grid.dim; ++d) {
+        const int64_t off = (P->slab && d == P->grid.dim - 1) ? P->row0 : 0;   // global index of local row 0
         for (int i = 0; i < P->geom.n[d]; ++i) {
-            const double x = ((double)i - P->grid.npml + 0.5) * h;
+            const double x = ((double)(i + off) - P->grid.npml + 0.5) * h;
             const cd a = inv_stretch(P, d, x);
             const cd bp = inv_stretch(P, d, x + 0.5 * h);
             const cd bm = inv_stretch(P, d, x - 0.5 * h);
@@ -184,19 +190,6 @@ static void build_coef_host(mxp_problem *P)
             P->coef_host[(size_t)(3 * d + 2) * nm + i] = make_double2(wc.real(), wc.imag());
         }
     }
-}
-
-// Representative indices of axis d: every PML index plus one interior index
-// (interior nodes share identical coefficients).
-static std::vector<int> axis_classes(const mxp_problem *P, int d)
-{
-    std::vector<int> out;
-    const int n = P->geom.n[d], p = P->grid.npml;
-    for (int i = 0; i < n; ++i) {
-        const bool pml = (i < p) || (i >= n - p);
-        if (pml || i == p) out.push_back(i);
-    }
-    return out;
 }
 
 static int effective_fuse(const mxp_problem *P)
@@ -275,17 +268,21 @@ static mxp_status upload_tau(mxp_problem *P)
 
 static void update_plans(mxp_problem *P)
 {
-    // per-axis coefficient classes (every PML index plus one interior index)
+    // per-axis coefficient classes (every PML index plus one interior index of
+    // the whole grid, so that every slab of a grid gets the same plan)
     AxisClasses cls[3];
-    const int nm = P->geom.nmax;
-    for (int d = 0; d < P->grid.dim; ++d)
-        for (int i : axis_classes(P, d)) {
-            const double2 wp = P->coef_host[(size_t)(3 * d) * nm + i];
-            const double2 wm = P->coef_host[(size_t)(3 * d + 1) * nm + i];
-            const double2 wc = P->coef_host[(size_t)(3 * d + 2) * nm + i];
-            cls[d].off.push_back(std::hypot(wp.x, wp.y) + std::hypot(wm.x, wm.y));
-            cls[d].wc.push_back(cd(wc.x, wc.y));
+    const double h = P->grid.h, ih2 = 1.0 / (h * h);
+    for (int d = 0; d < P->grid.dim; ++d) {
+        const int64_t n = P->grid.n_interior[d] + 2 * (int64_t)P->grid.npml, p = P->grid.npml;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!(i < p || i >= n - p || i == p)) continue;
+            const double x = ((double)i - p + 0.5) * h;
+            const cd a = inv_stretch(P, d, x), bp = inv_stretch(P, d, x + 0.5 * h), bm = inv_stretch(P, d, x - 0.5 * h);
+            const cd wp = a * bp * ih2, wm = a * bm * ih2;
+            cls[d].off.push_back(std::abs(wp) + std::abs(wm));
+            cls[d].wc.push_back(wp + wm);
         }
+    }
     const double w2 = P->prm.omega * P->prm.omega;
     const ShiftChoice sh = choose_shift(cls, P->grid.dim, w2 / (P->cmax * P->cmax), w2 / (P->cmin * P->cmin),
                                         P->prm.shift_s, P->prm.t);
@@ -748,6 +745,13 @@ static mxp_status retune(mxp_problem *P)
 {
     P->persist_cfg = -1;
     P->f3_cfg = -1;
+    if (P->slab) {
+        // a slab runs single steps through mxp_horner_step: no tiled kernels
+        P->fused_cfg = -1;
+        P->fused_cost = 1e30;
+        make_plans(P);
+        return MXP_OK;
+    }
     if (P->nfaces) {
         // the tiled sweeps assume zero ghosts; in 2D the persistent kernel carries
         // the face terms and is used whenever a configuration fits
@@ -2119,8 +2123,11 @@ mxp_status mxp_default_params(const mxp_grid *grid, double c_min, double ppw, mx
     return MXP_OK;
 }
 
-mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, void *cuda_stream,
-                      mxp_problem **out)
+// A problem on rows [row0, row0 + nrows) of the last axis of `grid` (the whole
+// grid when nrows < 0).  c_host covers those rows; crange (nullable) gives the
+// wave-speed range of the whole grid, which sets the shift and the Taylor plan.
+static mxp_status create_impl(const mxp_grid *grid, int64_t row0, int64_t nrows, const double *c_host,
+                              const double *crange, int device, void *cuda_stream, mxp_problem **out)
 {
     if (!grid || !c_host || !out) return fail(MXP_EINVAL, "NULL argument");
     *out = nullptr;
@@ -2134,8 +2141,15 @@ mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, vo
         const int64_t nd = grid->n_interior[d] + 2 * (int64_t)grid->npml;
         if (nd > (1 << 20)) return fail(MXP_EINVAL, "axis too long");
         n[d] = (int)nd;
-        ntot *= nd;
     }
+    const bool slab = nrows >= 0;
+    if (slab) {
+        const int last = grid->dim - 1;
+        if (row0 < 0 || nrows < 1 || row0 + nrows > n[last])
+            return fail(MXP_EINVAL, "slab rows must lie inside the last axis of the grid");
+        n[last] = (int)nrows;
+    }
+    for (int d = 0; d < grid->dim; ++d) ntot *= n[d];
     if (ntot > (int64_t)1 << 34) return fail(MXP_EINVAL, "grid too large");
     double cmin = 1e300, cmax = 0;
     for (int64_t i = 0; i < ntot; ++i) {
@@ -2143,6 +2157,13 @@ mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, vo
         if (!std::isfinite(v) || v <= 0) return fail(MXP_EINVAL, "wave speed must be finite and > 0 everywhere");
         cmin = std::min(cmin, v);
         cmax = std::max(cmax, v);
+    }
+    if (crange) {
+        if (!(crange[0] > 0) || !(crange[1] >= crange[0]) || !std::isfinite(crange[1]) || crange[0] > cmin ||
+            crange[1] < cmax)
+            return fail(MXP_EINVAL, "the global wave-speed range must be finite, positive and contain the slab's");
+        cmin = crange[0];
+        cmax = crange[1];
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -2152,13 +2173,16 @@ mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, vo
     P->device = device;
     P->stream = (cudaStream_t)cuda_stream;
     P->grid = *grid;
+    P->slab = slab ? 1 : 0;
+    P->row0 = slab ? row0 : 0;
     P->geom.dim = grid->dim;
     for (int d = 0; d < 3; ++d) P->geom.n[d] = n[d];
     P->geom.s1 = n[0];
     P->geom.s2 = (int64_t)n[0] * n[1];
     P->geom.ntot = ntot;
     P->geom.nmax = std::max(n[0], std::max(n[1], n[2]));
-    P->geom.fast = 1;
+    // the interior fast path of k_step tests local indices against npml: off for slabs
+    P->geom.fast = slab ? 0 : 1;
     P->geom.npml = grid->npml;
     P->geom.ih2 = 1.0 / (grid->h * grid->h);
     P->ntot = ntot;
@@ -2183,6 +2207,51 @@ mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, vo
     if (s == MXP_OK) s = retune(P);
     if (s != MXP_OK) return bail(s);
     *out = P;
+    return MXP_OK;
+}
+
+mxp_status mxp_create(const mxp_grid *grid, const double *c_host, int device, void *cuda_stream,
+                      mxp_problem **out)
+{
+    return create_impl(grid, 0, -1, c_host, nullptr, device, cuda_stream, out);
+}
+
+mxp_status mxp_create_slab(const mxp_grid *grid, int64_t row0, int64_t nrows, const double *c_slab_host,
+                           const double *c_range, int device, void *cuda_stream, mxp_problem **out)
+{
+    if (!c_range) return fail(MXP_EINVAL, "NULL argument");
+    return create_impl(grid, row0, nrows, c_slab_host, c_range, device, cuda_stream, out);
+}
+
+mxp_status mxp_horner_step(mxp_problem *P, const double *sigma, const double *gamma, const double *rho,
+                           const void *p_dev, const void *y_dev, const void *v_dev, void *out_dev)
+{
+    if (!P || !sigma || !rho || !p_dev || !out_dev || (v_dev && !gamma)) return fail(MXP_EINVAL, "NULL argument");
+    if (out_dev == p_dev || out_dev == y_dev || out_dev == v_dev)
+        return fail(MXP_EINVAL, "out must not alias p, y or v");
+    DeviceGuard guard(P->device);
+    StepScalars<double2> sc;
+    sc.zfac = make_double2(1.0, P->prm.shift_s);
+    sc.mu = P->mu;
+    sc.sigma = make_double2(sigma[0], sigma[1]);
+    sc.gamma = v_dev ? make_double2(gamma[0], gamma[1]) : make_double2(0.0, 0.0);
+    sc.rho = make_double2(rho[0], rho[1]);
+    set_faces<double2>(P, sc);
+    launch_step<double2>(P->geom, P->coef64, P->kappa64, sc, (const double2 *)p_dev, (const double2 *)y_dev,
+                         (const double2 *)v_dev, (double2 *)out_dev, P->stream);
+    P->passes += 1;
+    CK(cudaGetLastError());
+    return MXP_OK;
+}
+
+mxp_status mxp_get_plan(const mxp_problem *P, int which, double *mu, int *S, int *m)
+{
+    if (!P || !mu || !S || !m) return fail(MXP_EINVAL, "NULL argument");
+    if (which < 0 || which > 2) return fail(MXP_EINVAL, "which must be 0 (exp), 1 (psi_1) or 2 (psi_2)");
+    const TaylorPlan &pl = which == 2 ? P->plan_psi2 : which ? P->plan_psi : P->plan_exp;
+    *mu = P->mu;
+    *S = pl.S;
+    *m = pl.m;
     return MXP_OK;
 }
 
@@ -2255,6 +2324,7 @@ static mxp_status build_faces(mxp_problem *P)
 mxp_status mxp_set_boundary(mxp_problem *P, const int *bc)
 {
     if (!P || !bc) return fail(MXP_EINVAL, "NULL argument");
+    if (P->slab) return fail(MXP_EINVAL, "a slab problem runs mxp_horner_step and mxp_apply_operator only");
     for (int f = 0; f < 6; ++f) {
         if (bc[f] < MXP_BC_DIRICHLET || bc[f] > MXP_BC_ABSORBING) return fail(MXP_EINVAL, "unknown boundary condition");
         if (f >= 2 * P->grid.dim && bc[f] != MXP_BC_DIRICHLET)
@@ -2325,6 +2395,7 @@ int mxp_num_tile_configs(void) { return fused2d_num_cfgs(); }
 mxp_status mxp_selftest_barrier_timeout(mxp_problem *P)
 {
     if (!P) return fail(MXP_EINVAL, "NULL problem");
+    if (P->slab) return fail(MXP_EINVAL, "a slab problem runs mxp_horner_step and mxp_apply_operator only");
     DeviceGuard guard(P->device);
     CKS(ensure_base(P));
     CK(barrier_selftest(P->bar, P->stream));
@@ -2345,6 +2416,7 @@ mxp_status mxp_attach_cnn(mxp_problem *P, mxp_cnn *net, double accept_tol)
     if (!P) return fail(MXP_EINVAL, "NULL problem");
     if (net && !(accept_tol >= 0 && accept_tol <= 1)) return fail(MXP_EINVAL, "accept_tol must lie in [0, 1]");
     if (net && P->grid.dim != 2) return fail(MXP_EINVAL, "the learned stage is available for 2D problems");
+    if (P->slab) return fail(MXP_EINVAL, "a slab problem runs mxp_horner_step and mxp_apply_operator only");
     P->cnn = net;
     P->cnn_tol = accept_tol;
     return MXP_OK;
@@ -2393,6 +2465,7 @@ mxp_status mxp_apply_phi(mxp_problem *P, int which, const void *x_dev, void *y_d
 {
     if (!P || !x_dev || !y_dev) return fail(MXP_EINVAL, "NULL argument");
     if (which < 0 || which > 2) return fail(MXP_EINVAL, "which must be 0 (exp), 1 (psi_1) or 2 (psi_2)");
+    if (P->slab) return fail(MXP_EINVAL, "a slab problem runs mxp_horner_step and mxp_apply_operator only");
     DeviceGuard guard(P->device);
     CKS(ensure_base(P));
     const int64_t ps = phi_dispatch(P, which, (const double2 *)x_dev, (double2 *)y_dev, 0);
@@ -2407,6 +2480,7 @@ mxp_status mxp_apply_matexpre(mxp_problem *P, const void *r_dev, void *w_dev, mx
 {
     if (!P || !r_dev || !w_dev) return fail(MXP_EINVAL, "NULL argument");
     if (r_dev == w_dev) return fail(MXP_EINVAL, "r and w must not alias");
+    if (P->slab) return fail(MXP_EINVAL, "a slab problem runs mxp_horner_step and mxp_apply_operator only");
     DeviceGuard guard(P->device);
     return precond_apply(P, (const double2 *)r_dev, (double2 *)w_dev, st);
 }
@@ -2425,6 +2499,7 @@ mxp_status mxp_solve(mxp_problem *P, const void *b_dev, void *x_dev, const mxp_s
 {
     if (!P || !b_dev || !x_dev) return fail(MXP_EINVAL, "NULL argument");
     if (b_dev == x_dev) return fail(MXP_EINVAL, "b and x must not alias");
+    if (P->slab) return fail(MXP_EINVAL, "a slab problem runs mxp_horner_step and mxp_apply_operator only");
     CKS(check_opts(opts));
     DeviceGuard guard(P->device);
     return fgmres_solve(P, (const double2 *)b_dev, (double2 *)x_dev, opts, st);
@@ -2434,6 +2509,7 @@ mxp_status mxp_solve_host(mxp_problem *P, const void *b_host, void *x_host, cons
                           mxp_solve_stats *st)
 {
     if (!P || !b_host || !x_host) return fail(MXP_EINVAL, "NULL argument");
+    if (P->slab) return fail(MXP_EINVAL, "a slab problem runs mxp_horner_step and mxp_apply_operator only");
     CKS(check_opts(opts));
     DeviceGuard guard(P->device);
     const size_t bytes = (size_t)P->ntot * sizeof(double2);
@@ -2459,6 +2535,9 @@ mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs, const
         if (prob_of_rhs[r] < 0 || prob_of_rhs[r] >= nprob || !probs[prob_of_rhs[r]] || !b_dev[r] || !x_dev[r] ||
             b_dev[r] == x_dev[r])
             return fail(MXP_EINVAL, "invalid right-hand side entry");
+    for (int q = 0; q < nprob; ++q)
+        if (probs[q] && probs[q]->slab)
+            return fail(MXP_EINVAL, "a slab problem runs mxp_horner_step and mxp_apply_operator only");
     // group the right-hand sides by problem handle (the same handle may appear twice)
     std::vector<mxp_problem *> handles;
     std::vector<std::vector<int>> groups;

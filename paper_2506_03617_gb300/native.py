@@ -72,6 +72,13 @@ SIGNATURES = {
                               ct.POINTER(ct.c_void_p)]),
     "mxp_default_params": (ct.c_int, [ct.POINTER(Grid), ct.c_double, ct.c_double,
                                       ct.POINTER(Params)]),
+    "mxp_create_slab": (ct.c_int, [ct.POINTER(Grid), ct.c_int64, ct.c_int64, ct.POINTER(ct.c_double),
+                                   ct.POINTER(ct.c_double), ct.c_int, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    "mxp_horner_step": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
+                                   ct.POINTER(ct.c_double), ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                   ct.c_void_p]),
+    "mxp_get_plan": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int),
+                                ct.POINTER(ct.c_int)]),
     "mxp_set_params": (ct.c_int, [ct.c_void_p, ct.POINTER(Params)]),
     "mxp_get_params": (ct.c_int, [ct.c_void_p, ct.POINTER(Params)]),
     "mxp_apply_operator": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]),
@@ -198,6 +205,61 @@ class Problem:
         self._h = h_out
         if params is not None:
             self.set_params(**params)
+
+    @classmethod
+    def slab(cls, grid, row0, nrows, c_slab, c_range, params=None, device=0, stream=None):
+        """The problem on rows [row0, row0 + nrows) of the last axis of `grid`
+        (mxp_create_slab); c_slab: the wave speed of those rows; c_range: (min,
+        max) of c over the whole grid."""
+        import torch
+        self = cls.__new__(cls)
+        self._lib = load()
+        self.dim = grid.dim
+        self.n_interior = tuple(grid.ni)
+        self.npml = grid.npml
+        self.h = grid.h
+        n = list(grid.n)
+        n[-1] = int(nrows)
+        self.n = tuple(n)
+        self.n_total = int(np.prod(self.n))
+        self.device = int(device)
+        g = Grid()
+        g.dim = grid.dim
+        for d in range(3):
+            g.n_interior[d] = grid.ni[d] if d < grid.dim else 1
+        g.npml = grid.npml
+        g.h = grid.h
+        self._grid = g
+        c = np.ascontiguousarray(np.asarray(c_slab, dtype=np.float64).reshape(-1))
+        if c.size != self.n_total:
+            raise ValueError(f"slab medium has {c.size} values, the slab has {self.n_total}")
+        self.cmin = float(c_range[0])
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        rng = (ct.c_double * 2)(float(c_range[0]), float(c_range[1]))
+        h_out = ct.c_void_p()
+        _check(self._lib.mxp_create_slab(ct.byref(g), int(row0), int(nrows),
+                                         c.ctypes.data_as(ct.POINTER(ct.c_double)), rng, self.device,
+                                         _stream_handle(self.stream), ct.byref(h_out)))
+        self._h = h_out
+        if params is not None:
+            self.set_params(omega=params.omega, shift_s=params.shift, t=params.t, c_pml=params.cpml,
+                            fprtol=params.fprtol)
+        return self
+
+    def horner_step(self, sigma, p, y=None, v=None, gamma=0j, rho=1 + 0j, out=None):
+        """out = rho (y + sigma (A_s - mu) p + gamma v) (mxp_horner_step)."""
+        o = self.empty() if out is None else out
+        c2 = lambda z: (ct.c_double * 2)(complex(z).real, complex(z).imag)
+        _check(self._lib.mxp_horner_step(self._h, c2(sigma), c2(gamma), c2(rho), _ptr(p),
+                                         _ptr(y) if y is not None else None,
+                                         _ptr(v) if v is not None else None, _ptr(o)))
+        return o
+
+    def plan(self, which=0):
+        """(mu, S, m) of action `which` (mxp_get_plan)."""
+        mu, S, m = ct.c_double(0), ct.c_int(0), ct.c_int(0)
+        _check(self._lib.mxp_get_plan(self._h, int(which), ct.byref(mu), ct.byref(S), ct.byref(m)))
+        return float(mu.value), int(S.value), int(m.value)
 
     @classmethod
     def from_grid(cls, grid, c, params=None, **kw):

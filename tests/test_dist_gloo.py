@@ -136,3 +136,96 @@ def test_gather_rejects_missing_and_duplicate_units():
     with pytest.raises(RuntimeError):
         D.gather_by_index({5: 1}, 3)
     assert D.gather_by_index({1: "b", 0: "a"}, 2) == ["a", "b"]
+
+
+# ---------------------------------------------------------------- slab decomposition
+
+SLAB_GRID = I.Grid(2, (30, 40), 5)          # 40 x 50 unknowns: rows of 40 along y
+SLAB_HALO = 3
+
+
+def _slab_job():
+    import oracle
+    from paper_2506_03617_gb300 import native as N
+    g = SLAB_GRID
+    c = I.layered_grf(g, seed=I.SEED_BASE + 9200, corr_cells=3.0)
+    p = I.paper_params(g, c, ppw=10.0)
+    P = oracle.Problem.from_grid(g, c, p)
+    x = I.random_complex(g.n_total, 77)
+    S, m = N.taylor_plan(P.norm_inf_tA(True), 1e-12, 6.0, 1)      # host-only planner, shift mu = 0
+    return P, p, x, (0.0, S, m)
+
+
+def _oracle_slab_step(P, e0, e1):
+    """out = rho (y + sigma A_s p) on rows [e0, e1) with zero values beyond them
+    (what a slab problem's step computes, here through the oracle's operator)."""
+    import torch
+    g = SLAB_GRID
+    row = g.n[0]
+
+    def step(sigma, pv, yv, rho, out):
+        full = np.zeros(g.n_total, dtype=np.complex128)
+        full[e0 * row:e1 * row] = pv.numpy()
+        ap = P.apply(full, shifted=True)[e0 * row:e1 * row]
+        out.copy_(torch.from_numpy(rho * (yv.numpy() + sigma * ap)))
+    return step
+
+
+def _slab_worker(rank, world, port, q):
+    import oracle
+    import torch
+    import torch.distributed as dist
+    from paper_2506_03617_gb300 import dist as D
+    _init(rank, world, port)
+    oracle.set_threads(1)
+    P, p, x, plan = _slab_job()
+    g = SLAB_GRID
+    rows, row = g.n[-1], g.n[0]
+    bounds = D.slab_bounds(rows, world)
+    e0, e1 = D.slab_extended(bounds, rank, SLAB_HALO, rows)
+    r0, r1 = bounds[rank]
+    p0 = torch.zeros((e1 - e0) * row, dtype=torch.complex128)
+    p0[(r0 - e0) * row:(r1 - e0) * row] = torch.from_numpy(x[r0 * row:r1 * row])
+    bufs = [torch.zeros_like(p0), torch.zeros_like(p0)]
+    ex = D.SlabExchange(bounds, rank, SLAB_HALO, row, rows)
+    res = D.slab_exp_action([_oracle_slab_step(P, e0, e1)], plan, p.t, [p0], [bufs], ex, SLAB_HALO)[0]
+    owned = slice((r0 - e0) * row, (r1 - e0) * row)
+    dot = D.slab_dot(res, res, owned)
+    q.put((rank, r0, r1, res[owned].numpy().copy(), dot))
+    dist.destroy_process_group()
+
+
+def test_slab_decomposed_exp_action_matches_the_single_domain_oracle():
+    """Two gloo ranks each hold half of the grid's rows plus 3 halo rows, run the
+    sub-stepped Horner recurrence of exp(i t A_s) with a halo exchange every 3
+    steps and at every sub-step end, and together reproduce the oracle's exp
+    action on the whole grid; the allreduced dot equals the global one."""
+    P, p, x, plan = _slab_job()
+    ref = P.phi(0, x)[0]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    out = sorted((q.get(timeout=600) for _ in range(2)), key=lambda t: t[0])
+    for pr in procs:
+        pr.join(timeout=120)
+        assert pr.exitcode == 0
+    row = SLAB_GRID.n[0]
+    got = np.zeros_like(ref)
+    for _, r0, r1, vals, _ in out:
+        got[r0 * row:r1 * row] = vals
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-10
+    for *_, dot in out:
+        assert abs(dot - np.vdot(got, got)) <= 1e-12 * abs(np.vdot(got, got))
+
+
+def test_slab_bounds_cover_the_rows_once():
+    from paper_2506_03617_gb300 import dist as D
+    for n, w in ((50, 2), (51, 4), (7, 7)):
+        b = D.slab_bounds(n, w)
+        assert b[0][0] == 0 and b[-1][1] == n and all(b[k][1] == b[k + 1][0] for k in range(w - 1))
+        assert max(r1 - r0 for r0, r1 in b) - min(r1 - r0 for r0, r1 in b) <= 1
+    assert D.slab_extended(D.slab_bounds(50, 2), 0, 3, 50) == (0, 28)
+    assert D.slab_extended(D.slab_bounds(50, 2), 1, 3, 50) == (22, 50)
