@@ -882,7 +882,9 @@ def run_experiment(args):
         def rel(a, r):
             return float(torch.linalg.vector_norm(a - r) / torch.linalg.vector_norm(r))
 
-        for tol, th in [(1e-6, 4), (1e-5, 6), (1e-4, 6), (1e-3, 6), (1e-3, 8), (1e-4, 10)]:
+        plans = ([(1e-6, 4), (1e-5, 6), (1e-4, 6), (1e-3, 6), (1e-3, 8), (1e-4, 10)] if prec != "bf16s" else
+                 [(1e-6, 4), (1e-4, 4), (1e-3, 4), (1e-3, 3), (1e-6, 3), (1e-3, 5)])
+        for tol, th in plans:
             prob.set_params(prec=prec, exp_tol=tol, theta_max=th)
             e, ps = prob.apply_phi(0, xv)
             s1 = prob.apply_phi(1, xv)[0]
