@@ -187,6 +187,26 @@ mxp_status mxp_horner_step(mxp_problem *prob, const double *sigma, const double 
  * i t (A_s - mu) / S) v. */
 mxp_status mxp_get_plan(const mxp_problem *prob, int which, double *mu, int *S, int *m);
 
+/* Vector operations of a Krylov solve split over slabs (one per rank), on
+ * complex128 vectors of the problem's size (its unknowns; for a slab, the
+ * extended slab).  Both run on the problem's stream.
+ *
+ * mxp_vec_mdot: out_host[2i], out_host[2i + 1] = Re, Im of the sum over the
+ * rows [row_lo, row_hi) of the last axis (local row indices) of conj(V_i) w,
+ * for the k <= 64 vectors V_i = V_dev + i ldv (ldv in complex elements, at
+ * least the number of unknowns when k > 1).  FP64, deterministic.  A slab sums
+ * the rows it owns and the caller adds the ranks' results (one all-reduce).
+ * Synchronises the stream.
+ *
+ * mxp_vec_combine: y = beta y + sum_{i < k} coef_i V_i, complex scalars as
+ * {re, im} (beta[2], coef_host[2k]), 0 <= k <= 64; y must not alias a V_i.
+ * Asynchronous (the coefficients are copied before the call returns).
+ * MXP_EINVAL for out-of-range k, rows or ldv. */
+mxp_status mxp_vec_mdot(mxp_problem *prob, const void *V_dev, int64_t ldv, int k, const void *w_dev,
+                        int64_t row_lo, int64_t row_hi, double *out_host);
+mxp_status mxp_vec_combine(mxp_problem *prob, void *y_dev, const double *beta, const void *V_dev, int64_t ldv,
+                           int k, const double *coef_host);
+
 /* Fill *p with the paper's rules for a grid whose slowest speed is c_min and
  * `ppw` points per slowest wavelength: omega = 2 pi c_min / (ppw h),
  * freq = 1/(ppw h), s = 1/freq, t = 40 h^2 (0.4/freq^2 at ppw 10), C_pml 20,
@@ -278,6 +298,9 @@ mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs,
  * currently uses: -1 = unfused, else a configuration index whose fused step
  * count is returned in *fuse_k (nullable). */
 int mxp_num_tile_configs(void);
+
+/* Number of persistent 2D configurations (valid values of persist_cfg). */
+int mxp_num_persist_configs(void);
 int mxp_tile_config(const mxp_problem *prob, int *fuse_k);
 /* Persistent exp-action kernel in use (-1 = none) and its tile count. */
 int mxp_persist_config(const mxp_problem *prob, int *ntiles);

@@ -145,6 +145,7 @@ struct mxp_problem {
     void *hb[4] = {nullptr, nullptr, nullptr, nullptr};   // 16 bytes per unknown each
     double2 *rt = nullptr, *tmp = nullptr, *tmp2 = nullptr;
     double2 *bdev = nullptr, *xdev = nullptr;
+    double2 *vec_dev = nullptr;           // [128]: results of mxp_vec_mdot, coefficients of mxp_vec_combine
     Arnoldi inner, outer;
     KrylovScratch ks{};
     double *host_scal = nullptr;   // pinned, 8 doubles
@@ -2244,6 +2245,56 @@ mxp_status mxp_horner_step(mxp_problem *P, const double *sigma, const double *ga
     return MXP_OK;
 }
 
+static mxp_status ensure_vec(mxp_problem *P)
+{
+    if (!P->ks.partials) {
+        P->ks.grid = sm_count() * 4;
+        CK(cudaMalloc(&P->ks.partials, (size_t)P->ks.grid * kChunk * sizeof(double2)));
+    }
+    if (!P->vec_dev) CK(cudaMalloc(&P->vec_dev, 128 * sizeof(double2)));
+    return MXP_OK;
+}
+
+mxp_status mxp_vec_mdot(mxp_problem *P, const void *V_dev, int64_t ldv, int k, const void *w_dev, int64_t row_lo,
+                        int64_t row_hi, double *out_host)
+{
+    if (!P || !V_dev || !w_dev || !out_host) return fail(MXP_EINVAL, "NULL argument");
+    const int64_t nrow = P->geom.n[P->grid.dim - 1], row_len = P->ntot / nrow;
+    if (k < 1 || k > 64) return fail(MXP_EINVAL, "k must lie in [1, 64]");
+    if (k > 1 && ldv < P->ntot) return fail(MXP_EINVAL, "ldv must be at least the number of unknowns");
+    if (row_lo < 0 || row_hi > nrow || row_lo > row_hi) return fail(MXP_EINVAL, "rows outside the problem");
+    DeviceGuard guard(P->device);
+    CKS(ensure_vec(P));
+    if (row_hi == row_lo) {
+        for (int i = 0; i < 2 * k; ++i) out_host[i] = 0.0;
+        return MXP_OK;
+    }
+    const int64_t off = row_lo * row_len, len = (row_hi - row_lo) * row_len;
+    krylov_mdot((const double2 *)V_dev + off, ldv, k, (const double2 *)w_dev + off, len, P->vec_dev, 0, P->ks,
+                P->stream);
+    CK(cudaMemcpyAsync(out_host, P->vec_dev, (size_t)k * sizeof(double2), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    return MXP_OK;
+}
+
+mxp_status mxp_vec_combine(mxp_problem *P, void *y_dev, const double *beta, const void *V_dev, int64_t ldv, int k,
+                           const double *coef_host)
+{
+    if (!P || !y_dev || !beta || (k > 0 && (!V_dev || !coef_host))) return fail(MXP_EINVAL, "NULL argument");
+    if (k < 0 || k > 64) return fail(MXP_EINVAL, "k must lie in [0, 64]");
+    if (k > 1 && ldv < P->ntot) return fail(MXP_EINVAL, "ldv must be at least the number of unknowns");
+    DeviceGuard guard(P->device);
+    CKS(ensure_vec(P));
+    const int64_t n = P->ntot;
+    if (!(beta[0] == 1.0 && beta[1] == 0.0)) krylov_scale((double2 *)y_dev, make_double2(beta[0], beta[1]), n, P->stream);
+    if (k > 0) {
+        CK(cudaMemcpyAsync(P->vec_dev + 64, coef_host, (size_t)k * sizeof(double2), cudaMemcpyHostToDevice, P->stream));
+        krylov_maxpy((double2 *)y_dev, (const double2 *)V_dev, ldv, k, P->vec_dev + 64, 1.0, n, P->stream);
+    }
+    CK(cudaGetLastError());
+    return MXP_OK;
+}
+
 mxp_status mxp_get_plan(const mxp_problem *P, int which, double *mu, int *S, int *m)
 {
     if (!P || !mu || !S || !m) return fail(MXP_EINVAL, "NULL argument");
@@ -2391,6 +2442,8 @@ mxp_status mxp_get_params(const mxp_problem *P, mxp_params *p)
 int64_t mxp_num_unknowns(const mxp_problem *P) { return P ? P->ntot : 0; }
 
 int mxp_num_tile_configs(void) { return fused2d_num_cfgs(); }
+
+int mxp_num_persist_configs(void) { return persist2d_num_cfgs(); }
 
 mxp_status mxp_selftest_barrier_timeout(mxp_problem *P)
 {
@@ -2636,6 +2689,7 @@ void mxp_destroy(mxp_problem *P)
     tma3_destroy(P->tma3);
     cudaFree(P->rt); cudaFree(P->tmp); cudaFree(P->tmp2); cudaFree(P->bdev); cudaFree(P->xdev);
     cudaFree(P->ks.partials);
+    cudaFree(P->vec_dev);
     cudaFree(P->tau_dev);
     cudaFree(P->tau_psi_dev);
     cudaFree(P->wcoef_dev);

@@ -207,6 +207,20 @@ void krylov_add(double2 *out, const double2 *a, int64_t n, cudaStream_t st)
     k_add<<<grid_for(n, 256), 256, 0, st>>>(out, a, n);
 }
 
+__global__ void k_scale(double2 *__restrict__ w, double2 a, int64_t n)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = w[p];
+        w[p] = make_double2(a.x * v.x - a.y * v.y, a.x * v.y + a.y * v.x);
+    }
+}
+
+void krylov_scale(double2 *w, double2 a, int64_t n, cudaStream_t st)
+{
+    count_launch();
+    k_scale<<<grid_for(n, 256), 256, 0, st>>>(w, a, n);
+}
+
 void krylov_copy(double2 *out, const double2 *a, int64_t n, cudaStream_t st)
 {
     cudaMemcpyAsync(out, a, n * sizeof(double2), cudaMemcpyDeviceToDevice, st);

@@ -254,6 +254,7 @@ void krylov_scale_invnorm(double2 *w, const double2 *x, const double *nrm2sq_dev
 void krylov_sub(double2 *out, const double2 *a, const double2 *b, int64_t n, cudaStream_t st);
 void krylov_copy(double2 *out, const double2 *a, int64_t n, cudaStream_t st);
 void krylov_add(double2 *out, const double2 *a, int64_t n, cudaStream_t st);   // out += a
+void krylov_scale(double2 *w, double2 a, int64_t n, cudaStream_t st);     // w *= a
 void krylov_addvec(double2 *a, const double2 *b, int n, cudaStream_t st, const double *gate = nullptr);
 // kappa = omega^2 / c^2 in double and float
 void compute_kappa(const double *c, double omega, double *k64, float *k32, int64_t n,

@@ -79,6 +79,10 @@ SIGNATURES = {
                                    ct.c_void_p]),
     "mxp_get_plan": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int),
                                 ct.POINTER(ct.c_int)]),
+    "mxp_vec_mdot": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int, ct.c_void_p, ct.c_int64,
+                                ct.c_int64, ct.POINTER(ct.c_double)]),
+    "mxp_vec_combine": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_double), ct.c_void_p, ct.c_int64,
+                                   ct.c_int, ct.POINTER(ct.c_double)]),
     "mxp_set_params": (ct.c_int, [ct.c_void_p, ct.POINTER(Params)]),
     "mxp_get_params": (ct.c_int, [ct.c_void_p, ct.POINTER(Params)]),
     "mxp_apply_operator": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]),
@@ -115,6 +119,7 @@ SIGNATURES = {
     "mxp_selftest_barrier_timeout": (ct.c_int, [ct.c_void_p]),
     "mxp_kernel_launch_count": (ct.c_int64, []),
     "mxp_num_tile_configs": (ct.c_int, []),
+    "mxp_num_persist_configs": (ct.c_int, []),
     "mxp_tile_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_persist_config": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int)]),
     "mxp_persist_geometry": (ct.c_int, [ct.c_void_p] + [ct.POINTER(ct.c_int)] * 5),
@@ -254,6 +259,35 @@ class Problem:
                                          _ptr(y) if y is not None else None,
                                          _ptr(v) if v is not None else None, _ptr(o)))
         return o
+
+    def _rows(self, V):
+        """(pointer, leading dimension) of a vector or of a 2D tensor of vectors."""
+        import torch
+        if V.dim() == 1:
+            return _ptr(V), self.n_total
+        if not (V.is_cuda and V.dtype == torch.complex128 and V.stride(1) == 1 and V.shape[1] == self.n_total):
+            raise ValueError("V must hold complex128 CUDA rows of the problem's size")
+        return ct.c_void_p(V.data_ptr()), V.stride(0)
+
+    def vec_mdot(self, V, k, w, row_lo, row_hi):
+        """[sum over rows [row_lo, row_hi) of conj(V[i]) w for i < k] (mxp_vec_mdot);
+        V a 2D complex128 CUDA tensor (one vector per row) or one vector."""
+        out = (ct.c_double * (2 * k))()
+        vp, ld = self._rows(V)
+        _check(self._lib.mxp_vec_mdot(self._h, vp, int(ld), int(k), _ptr(w), int(row_lo), int(row_hi), out))
+        a = np.frombuffer(out, dtype=np.float64)
+        return a[0::2] + 1j * a[1::2]
+
+    def vec_combine(self, y, beta, V=None, coefs=()):
+        """y = beta y + sum_i coefs[i] V[i] (mxp_vec_combine); V as for vec_mdot."""
+        k = len(coefs)
+        b = (ct.c_double * 2)(complex(beta).real, complex(beta).imag)
+        cf = (ct.c_double * max(1, 2 * k))()
+        for i, z in enumerate(coefs):
+            cf[2 * i], cf[2 * i + 1] = complex(z).real, complex(z).imag
+        vp, ld = self._rows(V) if k else (None, self.n_total)
+        _check(self._lib.mxp_vec_combine(self._h, _ptr(y), b, vp, int(ld), int(k), cf))
+        return y
 
     def plan(self, which=0):
         """(mu, S, m) of action `which` (mxp_get_plan)."""

@@ -229,3 +229,82 @@ def test_slab_bounds_cover_the_rows_once():
         assert max(r1 - r0 for r0, r1 in b) - min(r1 - r0 for r0, r1 in b) <= 1
     assert D.slab_extended(D.slab_bounds(50, 2), 0, 3, 50) == (0, 28)
     assert D.slab_extended(D.slab_bounds(50, 2), 1, 3, 50) == (22, 50)
+
+
+# ------------------------------------------------- slab-decomposed FGMRES / Algorithm 1
+
+SOLVE_GRID = I.Grid(2, (22, 26), 5)
+SOLVE_HALO = 3
+
+
+def _solve_job():
+    import oracle
+    from paper_2506_03617_gb300 import native as N
+    g = SOLVE_GRID
+    c = I.layered_grf(g, seed=I.SEED_BASE + 9400, corr_cells=3.0)
+    p = I.paper_params(g, c, ppw=10.0, t_over_h2=10.0)
+    P = oracle.Problem.from_grid(g, c, p)
+    S, m = N.taylor_plan(P.norm_inf_tA(True), 1e-11, 6.0, 1)
+    params = dict(t=p.t, fprtol=p.fprtol, inner_restart=30, inner_maxit=400, inner_fixed=0, precond=0,
+                  neumann_n=0)
+    b = I.rhs_from_source(I.gaussian_source(g)).ravel()
+    return P, params, [(0.0, S, m)] * 3, b
+
+
+def _run_slab_solve(world, rank, exchange, allreduce):
+    import torch
+    from _slab_oracle import OracleSlab
+    from paper_2506_03617_gb300 import dist as D
+    P, params, plans, b = _solve_job()
+    g = SOLVE_GRID
+    rows, row = g.n[-1], g.n[0]
+    bounds = D.slab_bounds(rows, world)
+    e0, e1 = D.slab_extended(bounds, rank, SOLVE_HALO, rows)
+    r0, r1 = bounds[rank]
+    slab = OracleSlab(P, g, e0, e1, params, plans)
+    bs = torch.from_numpy(np.ascontiguousarray(b[e0 * row:e1 * row]))
+    xs = torch.zeros_like(bs)
+    solver = D.SlabSolver([slab], [(r0 - e0, r1 - e0)], exchange, allreduce, SOLVE_HALO)
+    st = solver.solve([bs], [xs], rtol=1e-6, restart=30, maxit=60)
+    return r0, r1, xs[(r0 - e0) * row:(r1 - e0) * row].numpy().copy(), st
+
+
+def _slab_solve_worker(rank, world, port, q):
+    import oracle
+    import torch.distributed as dist
+    from paper_2506_03617_gb300 import dist as D
+    _init(rank, world, port)
+    oracle.set_threads(1)
+    bounds = D.slab_bounds(SOLVE_GRID.n[-1], world)
+    ex = D.SlabExchange(bounds, rank, SOLVE_HALO, SOLVE_GRID.n[0], SOLVE_GRID.n[-1])
+    q.put((rank,) + _run_slab_solve(world, rank, ex, D.torch_allreduce))
+    dist.destroy_process_group()
+
+
+def test_slab_decomposed_solve_matches_one_domain():
+    """Algorithm 1 inside FGMRES(30) on a grid split into two slabs over gloo
+    ranks (halo 3, every dot summed over the ranks) takes the same outer and
+    inner iterations as the same driver on the whole grid, reaches the same
+    solution, and meets rtol 1e-6 in the oracle's true residual."""
+    import oracle
+    P, _, _, b = _solve_job()
+    oracle.set_threads(1)
+    _, _, x1, st1 = _run_slab_solve(1, 0, lambda vs: None, None)
+    assert st1["converged"] and st1["outer_iters"] > 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_solve_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    out = sorted((q.get(timeout=900) for _ in range(2)), key=lambda t: t[0])
+    for pr in procs:
+        pr.join(timeout=120)
+        assert pr.exitcode == 0
+    row = SOLVE_GRID.n[0]
+    x2 = np.zeros_like(x1)
+    for _, r0, r1, vals, st in out:
+        x2[r0 * row:r1 * row] = vals
+        assert (st["outer_iters"], st["inner_iters_total"]) == (st1["outer_iters"], st1["inner_iters_total"])
+    assert np.linalg.norm(x2 - x1) / np.linalg.norm(x1) < 1e-9
+    assert np.linalg.norm(b - P.apply(x2)) / np.linalg.norm(b) <= 1.000001e-6

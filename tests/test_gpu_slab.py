@@ -93,3 +93,38 @@ def test_slab_refuses_whole_grid_calls(native):
         native.Problem.slab(g, 20, 20, c[:20 * row], (1.0, 1.0), p)      # rows beyond the grid
     with pytest.raises(native.MxpError):
         native.Problem.slab(g, 0, 10, 2 * c[:10 * row], (1.0, 1.5), p)   # range misses the slab's speeds
+
+
+@pytest.mark.parametrize("world,halo", [(2, 3), (3, 2)])
+def test_slab_decomposed_solve_matches_single_domain(native, world, halo):
+    """Algorithm 1 inside FGMRES(30) with the grid in slabs (SlabSolver: slab
+    problems, halo copies between them, dots summed over the slabs) against the
+    library's single-domain complex128 solve: the same outer and inner
+    iteration counts, the same solution to 1e-8, and the oracle's true residual
+    at rtol."""
+    from paper_2506_03617_gb300 import dist as D
+    g = I.Grid(2, (48, 40), 8)
+    c = I.layered_grf(g, seed=I.SEED_BASE + 9500, corr_cells=4.0)
+    p = I.paper_params(g, c, ppw=10.0)
+    b = I.rhs_from_source(I.gaussian_source(g)).ravel()
+    G = native.Problem.from_grid(g, c, p)
+    G.set_params(prec="c128", exp_tol=1e-12)
+    x_ref, st_ref = G.solve(torch.from_numpy(b).cuda(), rtol=1e-6)
+    bounds, probs, row = _slabs(native, g, c, p, world, halo)
+    slabs = [S for S, _, _ in probs]
+    owned = [(r0 - e0, r1 - e0) for (S, e0, e1), (r0, r1) in zip(probs, bounds)]
+    bd = torch.from_numpy(b).cuda()
+    bs = [bd[e0 * row:e1 * row].clone() for _, e0, e1 in probs]
+    xs = [torch.zeros_like(v) for v in bs]
+    solver = D.SlabSolver(slabs, owned, D.LocalSlabExchange(bounds, halo, row, g.n[-1]), None, halo)
+    st = solver.solve(bs, xs, rtol=1e-6, restart=30, maxit=300)
+    torch.cuda.synchronize()
+    x = torch.empty_like(bd)
+    for (S, e0, e1), (r0, r1), v in zip(probs, bounds, xs):
+        x[r0 * row:r1 * row] = v[(r0 - e0) * row:(r1 - e0) * row]
+    assert st["converged"]
+    assert (st["outer_iters"], st["inner_iters_total"]) == (st_ref["outer_iters"], st_ref["inner_iters_total"])
+    xh, xr = x.cpu().numpy(), x_ref.cpu().numpy()
+    assert np.linalg.norm(xh - xr) / np.linalg.norm(xr) < 1e-8
+    P = oracle.Problem.from_grid(g, c, p)
+    assert np.linalg.norm(b - P.apply(xh)) / np.linalg.norm(b) <= 1.000001e-6
