@@ -92,7 +92,7 @@ def test_low_precision_phi_with_faces(native, prec):
         check(base[which], ref, grid, TOL_POINTWISE[prec], what=f"faces per-point phi{which} {prec}",
               mask=_mask(grid))
     ran = set()
-    for cfg in range(9):
+    for cfg in range(native.load().mxp_num_persist_configs()):
         G.set_params(persist_cfg=cfg)
         if G.persist_config()[0] != cfg:
             continue

@@ -28,7 +28,6 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-N_PCFG = 9
 RAN = {}     # (action, prec) -> configurations that ran on some grid
 
 
@@ -46,7 +45,7 @@ def test_persistent_matches_per_pass_and_oracle(native, grid, prec):
     base = G.apply_phi(0, xd)[0].cpu().numpy()
     ref = P.phi(0, x)[0]
     ran = RAN.setdefault(("exp", prec), set())
-    for cfg in range(N_PCFG):
+    for cfg in range(native.load().mxp_num_persist_configs()):
         G.set_params(fuse_k=0, persist_cfg=cfg)
         if G.persist_config()[0] != cfg:
             continue                          # the grid does not fit this configuration
@@ -104,7 +103,7 @@ def test_persistent_psi1_matches_per_pass_and_oracle(native, grid, prec):
     base = G.apply_phi(1, xd)[0].cpu().numpy()
     ref = P.phi(1, x)[0]
     ran = RAN.setdefault(("psi1", prec), set())
-    for cfg in range(N_PCFG):
+    for cfg in range(native.load().mxp_num_persist_configs()):
         G.set_params(fuse_k=0, persist_cfg=cfg)
         if G.persist_config()[0] != cfg:
             continue
@@ -122,11 +121,10 @@ def test_persistent_psi1_matches_per_pass_and_oracle(native, grid, prec):
     check(w.cpu().numpy(), w_ref, grid, TOL_LOW[prec], what=f"psi2-variant apply {prec}")
 
 
-def test_every_configuration_ran():
+def test_every_configuration_ran(native):
     """No configuration was skipped everywhere: each one, for both storage types
     and both actions, met the oracle on at least one grid above."""
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
+    every = set(range(native.load().mxp_num_persist_configs()))
     for key in [("exp", "c64"), ("exp", "bf16s"), ("psi1", "c64"), ("psi1", "bf16s")]:
-        assert RAN.get(key, set()) == set(range(N_PCFG)), (key, sorted(RAN.get(key, set())))
+        assert RAN.get(key, set()) == every, (key, sorted(RAN.get(key, set())))
 
