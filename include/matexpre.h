@@ -280,15 +280,24 @@ mxp_status mxp_solve_host(mxp_problem *prob, const void *b_host, void *x_host,
 
 /* Many right-hand sides over several problems in one call.  Right-hand side r
  * belongs to problem probs[prob_of_rhs[r]]; b_dev[r], x_dev[r] are its vectors
- * on that problem's device.  The sources of one problem advance in lockstep:
- * their outer FGMRES and inner GMRES iterations run side by side and every
- * exp / psi_1 action of the active sources is one sweep launch per pass over
- * the batch, replayed from a captured CUDA graph; converged sources leave the
- * batch.  Different problems (grid sizes, media) are solved concurrently, one
- * host thread each; their kernels overlap on the GPU when the problems were
- * created on different streams.  Requires precond = 0; the inner GMRES stops
- * after inner_restart iterations if fprtol is not met.  per_rhs (nullable) has
- * nrhs entries.  Returns MXP_ENOCONV if some source reached maxit. */
+ * on that problem's device.  Scheduling:
+ *  - 2D problems in MXP_C64 or MXP_BF16S without faces (Algorithm 1) with
+ *    fewer than 2^20 unknowns form one group on one device: the sources of all
+ *    of them advance in lockstep (outer FGMRES and inner GMRES side by side),
+ *    every pass of their exp / psi_1 actions is one launch over all active
+ *    sources, converged sources are masked on the device, and each action's
+ *    pass sequence is replayed from a captured CUDA graph;
+ *  - a 2D problem whose actions run on the persistent kernel and that has at
+ *    least 2^20 unknowns solves its sources one after another with the
+ *    single-source FGMRES (as mxp_solve): there the persistent kernel fills the
+ *    GPU and the lockstep batch would be slower;
+ *  - any other problem advances its own sources in lockstep, one host thread
+ *    per problem, concurrently with the group (kernels overlap when the
+ *    problems were created on different streams); problems whose actions run on
+ *    the persistent kernel run after that, one at a time.
+ * The lockstep paths require precond = 0, and their inner GMRES stops after
+ * inner_restart iterations if fprtol is not met.  per_rhs (nullable) has nrhs
+ * entries.  Returns MXP_ENOCONV if some source reached maxit. */
 mxp_status mxp_solve_batch(mxp_problem *const *probs, int nprob, int nrhs,
                            const int *prob_of_rhs, const void *const *b_dev,
                            void *const *x_dev, const mxp_solve_opts *opts,

@@ -163,3 +163,41 @@ def test_grouped_solve_of_mixed_grid_sizes(native, prec):
         for i, x1 in zip(mine, xs1):
             assert _rel(xs[i].cpu().numpy(), x1.cpu().numpy()) < 1e-4
     assert grouped_launches < 0.8 * alone, (grouped_launches, alone)
+
+
+def test_large_problem_in_a_batch_solves_its_sources_one_by_one(native):
+    """A 2D problem on the persistent kernel with at least 2^20 unknowns (the
+    1088^2 layered workload) solves its sources one after another inside
+    mxp_solve_batch, while a small problem in the same call keeps the lockstep
+    path: each large source gives exactly its single-source solve (same outer
+    and inner counts, same solution), and every source meets the oracle's true
+    residual."""
+    g, c, p = I.config_2d_layered()
+    G = native.Problem.from_grid(g, c, p)
+    G.set_params(prec="c64", exp_tol=1e-3, theta_max=6.0)
+    assert G.persist_config()[0] >= 0 and g.n_total >= 1 << 20
+    gs = I.Grid(2, (64, 64), 8)
+    cs = I.layered_grf(gs, seed=I.SEED_BASE + 4600, corr_cells=4.0)
+    ps = I.paper_params(gs, cs, ppw=10.0)
+    Gs = native.Problem.from_grid(gs, cs, ps)
+    Gs.set_params(prec="c64", exp_tol=1e-6)
+    big = [I.rhs_from_source(I.gaussian_source(g, center=ctr)).ravel()
+           for ctr in I.random_centers(g, 2, seed=I.SEED_BASE + 4610)]
+    small = [I.rhs_from_source(I.gaussian_source(gs, center=ctr)).ravel()
+             for ctr in I.random_centers(gs, 2, seed=I.SEED_BASE + 4620)]
+    bs = [torch.from_numpy(b).cuda() for b in big + small]
+    xs = [G.empty(), G.empty(), Gs.empty(), Gs.empty()]
+    stats = native.solve_batch([G, Gs], [0, 0, 1, 1], bs, xs, rtol=1e-6, maxit=300)
+    torch.cuda.synchronize()
+    P = oracle.Problem.from_grid(g, c, p)
+    Ps = oracle.Problem.from_grid(gs, cs, ps)
+    for i, b in enumerate(big):
+        x1, st1 = G.solve(bs[i], rtol=1e-6, maxit=300)
+        assert (stats[i]["outer_iters"], stats[i]["inner_iters_total"]) == (st1["outer_iters"], st1["inner_iters_total"])
+        xh = xs[i].cpu().numpy()
+        assert _rel(xh, x1.cpu().numpy()) < 1e-12
+        assert np.linalg.norm(b - P.apply(xh)) / np.linalg.norm(b) <= 1.000001e-6
+    for i, b in enumerate(small):
+        assert stats[2 + i]["converged"]
+        xh = xs[2 + i].cpu().numpy()
+        assert np.linalg.norm(b - Ps.apply(xh)) / np.linalg.norm(b) <= 1.000001e-6
