@@ -84,6 +84,23 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks,
 // 0 poll one neighbour each (lane 4 is the tile itself), so the wait costs one
 // L2 round trip when the neighbours are already there.  Bounded polling: on
 // timeout the error word is set and the caller stops.
+// The epoch word is written with release semantics after the CTA barrier (so
+// the strips every thread of the CTA stored before it are visible first) and
+// read with acquire semantics before the closing CTA barrier (so the ring loads
+// that follow it see the neighbours' strips): the ordering of a fence on each
+// side without a full fence.
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ bool neighbour_sync(unsigned *bar, int bx, int by, int ntx, int nty,
                                                unsigned epoch)
 {
@@ -91,18 +108,15 @@ __device__ __forceinline__ bool neighbour_sync(unsigned *bar, int bx, int by, in
     __syncthreads();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        volatile unsigned *flags = bar + 4;
+        const unsigned *flags = bar + 4;
         volatile unsigned *verr = bar + 2;
-        if (lane == 0) {
-            __threadfence();
-            atomicExch(bar + 4 + (by * ntx + bx) * kPersistFlagStride, epoch);
-        }
+        if (lane == 0) st_release_gpu(bar + 4 + (by * ntx + bx) * kPersistFlagStride, epoch);
         int ok = 1;
         if (lane < 9 && lane != 4) {
             const int nx = bx + lane % 3 - 1, ny = by + lane / 3 - 1;
             if (nx >= 0 && ny >= 0 && nx < ntx && ny < nty) {
                 long long it = 0;
-                while (flags[(ny * ntx + nx) * kPersistFlagStride] < epoch) {
+                while (ld_acquire_gpu(flags + (ny * ntx + nx) * kPersistFlagStride) < epoch) {
                     if (++it > kNeighbourPollLimit || *verr != 0u) {
                         atomicExch(bar + 2, 1u);
                         ok = 0;
@@ -112,7 +126,6 @@ __device__ __forceinline__ bool neighbour_sync(unsigned *bar, int bx, int by, in
             }
         }
         ok = __all_sync(0xffffffffu, ok);
-        __threadfence();
         if (lane == 0) s_ok2 = ok && (*verr == 0u);
     }
     __syncthreads();
@@ -351,15 +364,35 @@ __global__ void __launch_bounds__(BX *BG, 1) k_persist2d(PersistArgs a, const S 
 // One Taylor-Horner step over a thread's R rows of its two columns (the body of
 // k_persist2d_x2): all shared loads of a chunk of CH rows are issued before its
 // arithmetic, then the chunk's results are stored.
-template <int R, int CH, int PX, int BXH>
+// Shared-memory index of the thread's column l (0: its first, 1: its second
+// column) in region row ry.  Interleaved rows hold the cells in order,
+// (ry + 1) PX + cx + 2; split rows hold all first columns of the column pairs,
+// then all second columns, each half with one zero cell on both sides, so that
+// the west neighbour (the second column of the thread to the left) and the east
+// neighbour (the first column of the thread to the right) are contiguous over
+// the lanes of a warp: two shared-memory wavefronts per load instead of four.
+template <bool SPLIT, int PX, int BXH>
+__device__ __forceinline__ int x2_cell(int ry, int tx, int l)
+{
+    return SPLIT ? (ry + 1) * PX + (l ? BXH + 3 : 1) + tx : (ry + 1) * PX + 2 * tx + l + 2;
+}
+
+template <int R, int CH, int PX, int BXH, bool SPLIT>
 __device__ __forceinline__ void x2_step_rows(const float2 *__restrict__ src, float2 *__restrict__ dst,
                                              const float2 *__restrict__ cy, const float2 *__restrict__ ks,
                                              int r0, int RH, int cx0, int tx, const float2 (&wpx)[2],
                                              const float2 (&wmx)[2], const float2 (&wcx)[2], float2 zh,
                                              float tau, const float2 (&y0r)[R], const float2 (&y1r)[R])
 {
-    float4 up = *reinterpret_cast<const float4 *>(src + r0 * PX + cx0 + 2);
-    float4 cen = *reinterpret_cast<const float4 *>(src + (r0 + 1) * PX + cx0 + 2);
+    auto ld_pair = [&](int ry) -> float4 {     // both columns of region row ry
+        if (SPLIT) {
+            const float2 lo = src[x2_cell<true, PX, BXH>(ry, tx, 0)], hi = src[x2_cell<true, PX, BXH>(ry, tx, 1)];
+            return make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+        return *reinterpret_cast<const float4 *>(src + (ry + 1) * PX + cx0 + 2);
+    };
+    float4 up = ld_pair(r0 - 1);
+    float4 cen = ld_pair(r0);
 #pragma unroll
     for (int c = 0; c < R; c += CH) {
         if (r0 + c >= RH) break;                 // uniform across the row group
@@ -369,9 +402,14 @@ __device__ __forceinline__ void x2_step_rows(const float2 *__restrict__ src, flo
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
             const int ry = r0 + c + j;
-            dn[j] = *reinterpret_cast<const float4 *>(src + (ry + 2) * PX + cx0 + 2);
-            wl[j] = src[(ry + 1) * PX + cx0 + 1];
-            er[j] = src[(ry + 1) * PX + cx0 + 4];
+            dn[j] = ld_pair(ry + 1);
+            if (SPLIT) {
+                wl[j] = src[x2_cell<true, PX, BXH>(ry, tx, 1) - 1];
+                er[j] = src[x2_cell<true, PX, BXH>(ry, tx, 0) + 1];
+            } else {
+                wl[j] = src[(ry + 1) * PX + cx0 + 1];
+                er[j] = src[(ry + 1) * PX + cx0 + 4];
+            }
             kk[j] = ks[ry * BXH + tx];
         }
 #pragma unroll
@@ -419,7 +457,12 @@ __device__ __forceinline__ void x2_step_rows(const float2 *__restrict__ src, flo
         }
 #pragma unroll
         for (int j = 0; j < CH; ++j)
-            *reinterpret_cast<float4 *>(dst + (r0 + c + j + 1) * PX + cx0 + 2) = o[j];
+            if (SPLIT) {
+                dst[x2_cell<true, PX, BXH>(r0 + c + j, tx, 0)] = make_float2(o[j].x, o[j].y);
+                dst[x2_cell<true, PX, BXH>(r0 + c + j, tx, 1)] = make_float2(o[j].z, o[j].w);
+            } else {
+                *reinterpret_cast<float4 *>(dst + (r0 + c + j + 1) * PX + cx0 + 2) = o[j];
+            }
     }
 }
 
@@ -433,7 +476,7 @@ __device__ __forceinline__ void x2_step_rows(const float2 *__restrict__ src, flo
 // by one cell per step, which the K-cell ring absorbs.  FACES = true adds the
 // ghost-point face terms as k_persist2d does (a separate instantiation, so the
 // face-free kernel keeps its register allocation).
-template <typename S, int K, int BXH, int BG, int R, int CH, bool FACES>
+template <typename S, int K, int BXH, int BG, int R, int CH, bool FACES, bool SPLIT>
 __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, const S *__restrict__ x,
                                                              S *__restrict__ ex0,
                                                              S *__restrict__ ex1,
@@ -513,7 +556,7 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
                 facemask[l] |= 1u << r;
             if (in) {
                 inmask[l] |= 1u << r;
-                b0[(ry + 1) * PX + cx0 + l + 2] = pv[l];
+                b0[x2_cell<SPLIT, PX, BXH>(ry, tx, l)] = pv[l];
                 const int cx = cx0 + l;
                 const bool intile = cx >= K && cx < K + a.txo && ry >= K && ry < K + a.tyo;
                 if (intile) {
@@ -535,7 +578,7 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
             float2 *dst = (s & 1) ? b0 : b1;
             const float tau = a.tau[pass * K + s];
             const int r0 = grp * R;
-            x2_step_rows<R, CH, PX, BXH>(src, dst, cy, ks, r0, RH, cx0, tx, wpx, wmx, wcx, zh, tau, y0r, y1r);
+            x2_step_rows<R, CH, PX, BXH, SPLIT>(src, dst, cy, ks, r0, RH, cx0, tx, wpx, wmx, wcx, zh, tau, y0r, y1r);
             if (FACES && (facemask[0] | facemask[1])) {
                 // boundary rows of a ghost-point face: q gains face * p on those cells
 #pragma unroll
@@ -549,7 +592,7 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
                             if (a.face[1] && gxl == n0 - 1) f = cadd(f, a.face[1][gy]);
                             if (a.face[2] && gy == 0) f = cadd(f, a.face[2][gxl]);
                             if (a.face[3] && gy == n1 - 1) f = cadd(f, a.face[3][gxl]);
-                            const int ci = (ry + 1) * PX + cx0 + l + 2;
+                            const int ci = x2_cell<SPLIT, PX, BXH>(ry, tx, l);
                             const float2 fp = cmul(f, src[ci]);
                             dst[ci] = make_float2(fmaf(-tau, fp.y, dst[ci].x), fmaf(tau, fp.x, dst[ci].y));
                         }
@@ -567,7 +610,7 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
 #pragma unroll
                 for (int l = 0; l < 2; ++l)
                     if ((tilemask[l] >> r) & 1u) {
-                        float2 &cell = b0[(ry + 1) * PX + cx0 + l + 2];
+                        float2 &cell = b0[x2_cell<SPLIT, PX, BXH>(ry, tx, l)];
                         cell = cadd(cell, cmul(cj, St<S>::ld(w, (int64_t)(gy0 + ry) * n0 + gx[l])));
                     }
             }
@@ -580,7 +623,7 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
 #pragma unroll
             for (int l = 0; l < 2; ++l)
                 if ((stripmask[l] >> r) & 1u)
-                    St<S>::st(ex, (int64_t)(gy0 + ry) * n0 + gx[l], b0[(ry + 1) * PX + cx0 + l + 2]);
+                    St<S>::st(ex, (int64_t)(gy0 + ry) * n0 + gx[l], b0[x2_cell<SPLIT, PX, BXH>(ry, tx, l)]);
         }
         alive = neighbour_sync(a.bar, bx, by, a.ntx, a.nty, (unsigned)(pass + 1));
         if (!alive) break;
@@ -603,7 +646,7 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
                 }
 #pragma unroll
                 for (int r = 0; r < R; ++r)
-                    if ((ring >> r) & 1u) b0[(grp * R + r + 1) * PX + cx0 + l + 2] = rv[r];
+                    if ((ring >> r) & 1u) b0[x2_cell<SPLIT, PX, BXH>(grp * R + r, tx, l)] = rv[r];
             }
         }
         __syncthreads();
@@ -611,8 +654,8 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int ry = grp * R + r;
-                if ((inmask[0] >> r) & 1u) y0r[r] = b0[(ry + 1) * PX + cx0 + 2];
-                if ((inmask[1] >> r) & 1u) y1r[r] = b0[(ry + 1) * PX + cx0 + 3];
+                if ((inmask[0] >> r) & 1u) y0r[r] = b0[x2_cell<SPLIT, PX, BXH>(ry, tx, 0)];
+                if ((inmask[1] >> r) & 1u) y1r[r] = b0[x2_cell<SPLIT, PX, BXH>(ry, tx, 1)];
             }
         }
     }
@@ -623,7 +666,7 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
 #pragma unroll
             for (int l = 0; l < 2; ++l)
                 if ((tilemask[l] >> r) & 1u)
-                    St<S>::st(out, (int64_t)(gy0 + ry) * n0 + gx[l], cmul(a.rho, b0[(ry + 1) * PX + cx0 + l + 2]));
+                    St<S>::st(out, (int64_t)(gy0 + ry) * n0 + gx[l], cmul(a.rho, b0[x2_cell<SPLIT, PX, BXH>(ry, tx, l)]));
         }
     }
 }
@@ -634,11 +677,12 @@ struct PCfg {
     int faces;       // adds ghost-point face terms
 };
 // Configuration 9 is configuration 6 with the shared loads of 7 rows (instead of 2)
-// issued ahead of their arithmetic (more loads in flight per thread, 160 registers).
+// issued ahead of their arithmetic (more loads in flight per thread, 160 registers);
+// configuration 10 is 9 with split rows (x2_cell).
 static const PCfg kPCfgs[] = {{2, 128, 4, 18, 0, 1}, {4, 96, 4, 28, 0, 1}, {4, 96, 8, 14, 0, 1},
                                {4, 96, 9, 12, 0, 1},  {2, 128, 8, 10, 0, 1}, {6, 96, 4, 28, 0, 1},
                                {6, 96, 8, 14, 1, 0},  {4, 96, 8, 14, 1, 0},  {6, 96, 8, 14, 1, 1},
-                               {6, 96, 8, 14, 1, 0}};
+                               {6, 96, 8, 14, 1, 0},  {6, 96, 8, 14, 1, 0}};
 constexpr int kNumP = sizeof(kPCfgs) / sizeof(kPCfgs[0]);
 
 int persist2d_num_cfgs() { return kNumP; }
@@ -652,8 +696,8 @@ static void *kernel_ptr() { return (void *)k_persist2d<S, K, BX, BG, R, (R % 4 =
 template <int R>
 constexpr int chunk_rows() { return (R % 4 == 0) ? 4 : (R % 2 == 0) ? 2 : 1; }
 
-template <typename S, int K, int BX, int BG, int R, bool F, int CH = chunk_rows<R>()>
-static void *kernel_ptr_x2() { return (void *)k_persist2d_x2<S, K, BX / 2, BG, R, CH, F>; }
+template <typename S, int K, int BX, int BG, int R, bool F, int CH = chunk_rows<R>(), bool SPLIT = false>
+static void *kernel_ptr_x2() { return (void *)k_persist2d_x2<S, K, BX / 2, BG, R, CH, F, SPLIT>; }
 
 template <typename S, int K, int BX, int BG, int R>
 static size_t smem_bytes_x2()
@@ -682,7 +726,8 @@ static void cfg_info(int id, void **fn, size_t *smem)
     case 6: *fn = kernel_ptr_x2<S, 6, 96, 8, 14, false>(); *smem = smem_bytes_x2<S, 6, 96, 8, 14>(); break;
     case 7: *fn = kernel_ptr_x2<S, 4, 96, 8, 14, false>(); *smem = smem_bytes_x2<S, 4, 96, 8, 14>(); break;
     case 8: *fn = kernel_ptr_x2<S, 6, 96, 8, 14, true>(); *smem = smem_bytes_x2<S, 6, 96, 8, 14>(); break;
-    default: *fn = kernel_ptr_x2<S, 6, 96, 8, 14, false, 7>(); *smem = smem_bytes_x2<S, 6, 96, 8, 14>(); break;
+    case 9: *fn = kernel_ptr_x2<S, 6, 96, 8, 14, false, 7>(); *smem = smem_bytes_x2<S, 6, 96, 8, 14>(); break;
+    default: *fn = kernel_ptr_x2<S, 6, 96, 8, 14, false, 7, true>(); *smem = smem_bytes_x2<S, 6, 96, 8, 14>(); break;
     }
 }
 
