@@ -3,15 +3,16 @@
 //
 // Each CTA owns one tile of the grid for the whole action.  The tile plus a
 // K-cell ring lives in shared memory (two ping-pong buffers); y (the sub-step
-// start vector) and kappa stay in registers.  One pass = K Horner steps on
-// the region; afterwards the tile interior is exact, the CTA publishes the
-// K-wide strips along its tile edges to a global exchange buffer, all CTAs meet
-// at a grid barrier, and each CTA refreshes its ring from its neighbours'
-// strips.  Global traffic per pass is only these strips (L2-resident), and
-// there is one launch per action instead of one per pass.
+// start vector) stays in registers.  One pass = K Horner steps on the region;
+// afterwards the tile interior is exact, the CTA publishes the K-wide strips
+// along its tile edges to a global exchange buffer and posts its pass number
+// (epoch), waits until its eight neighbours have posted theirs (point-to-point,
+// no grid-wide barrier), and refreshes its ring from their strips.  Global
+// traffic per pass is only these strips (L2-resident), and there is one launch
+// per action instead of one per pass.
 //
-// The grid barrier spins with a bounded iteration count; on timeout it sets an
-// error flag and every CTA leaves the pass loop, so the kernel always ends.
+// Every wait polls a bounded number of times; on timeout it sets an error word
+// and every CTA leaves the pass loop, so the kernel always ends.
 // Co-residency of all CTAs is guaranteed by the cooperative launch (the launch
 // fails instead of deadlocking when the grid does not fit).
 #include <algorithm>
