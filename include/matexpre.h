@@ -40,7 +40,7 @@ typedef enum {
     MXP_ENOMEM = 2,       /* device or host allocation failed */
     MXP_ECUDA = 3,        /* a CUDA runtime call failed */
     MXP_ENOCONV = 4,      /* iteration limit reached before the tolerance */
-    MXP_EBREAKDOWN = 5,   /* Krylov breakdown that is not a lucky one */
+    MXP_EBREAKDOWN = 5,   /* reserved: the solvers stop at h_{j+1,j} = 0 (a lucky breakdown) and never return it */
     MXP_ENAN = 6,         /* NaN or Inf met in a residual */
     MXP_ETIMEOUT = 7      /* a bounded device-side wait gave up */
 } mxp_status;
