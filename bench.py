@@ -828,7 +828,9 @@ def run_experiment(args):
         oracle.set_threads(ncores)
     elif args.experiment == "c4":
         # 2D: 64 sources on 8 media (3 x 288^2, 3 x 544^2, 2 x 1088^2 unknowns) in
-        # one mxp_solve_batch call: one group, every pass one launch over all of them
+        # one mxp_solve_batch call (the small media in one lockstep group, the
+        # 1088^2 media source by source); then the first source of every medium
+        # solved with FP64 actions, and the batched solution's error against it
         media = I.config_batched_2d()
         probs, pofr, bs, xs, meta = [], [], [], [], []
         for k, (g, c, p, centres) in enumerate(media):
@@ -856,6 +858,19 @@ def run_experiment(args):
                           "all_converged": all(q["converged"] for q in st),
                           "max_true_relres": max(q["true_relres"] for q in st),
                           "max_time_to_1e-6_s": max(q["seconds"] for q in st)}), flush=True)
+        for k, G in enumerate(probs):
+            i = next(r for r, kk in enumerate(pofr) if kk == k)
+            G.set_params(prec="c128", **plan_for("c128", args))
+            x64 = G.empty()
+            _, s64 = G.solve(bs[i], x64, rtol=1e-6, maxit=300)
+            print(json.dumps({"experiment": "c4", "part": "2d fp64 check", "medium": k, "source": 0,
+                              "unknowns": meta[i][2], "fp64_outer": s64["outer_iters"],
+                              "fp64_seconds": s64["seconds"],
+                              "solution_rel_err_vs_fp64_gpu":
+                                  float(torch.linalg.vector_norm(xs[i] - x64) / torch.linalg.vector_norm(x64))}),
+                  flush=True)
+            G.set_params(prec=prec, **plan_for(prec, args))
+            del x64
         del probs, bs, xs
         torch.cuda.empty_cache()
         if args.c4_3d_waves > 0:

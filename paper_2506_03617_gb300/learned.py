@@ -102,19 +102,33 @@ def load(net, path):
     return theta
 
 
+_FP64_SOLUTIONS = {}
+
+
 def evaluate(net, n_interior=1024, npml=32, seeds=(0,), accept_tol=0.5,
              seed_base=I.SEED_BASE + 6000, rtol=1e-6):
-    """FGMRES with and without the learned stage on held-out media."""
+    """FGMRES with and without the learned stage on held-out media, each
+    solution's error against the solve with FP64 actions."""
     import torch
     rows = []
     for s in seeds:
         g, c, p, G = _problem(n_interior, npml, seed_base + s)
         b = torch.from_numpy(I.rhs_from_source(I.gaussian_source(g)).ravel()).cuda()
         torch.cuda.synchronize()
-        _, st0 = G.solve(b, rtol=rtol, maxit=200)
+        x0, st0 = G.solve(b, rtol=rtol, maxit=200)
         N.attach_cnn(G, net, accept_tol)
-        _, st1 = G.solve(b, rtol=rtol, maxit=200)
+        x1, st1 = G.solve(b, rtol=rtol, maxit=200)
         N.attach_cnn(G, None)
+        key = (n_interior, npml, seed_base + s, rtol)
+        if key not in _FP64_SOLUTIONS:          # one FP64 solve per held-out medium
+            prm = G.get_params()
+            G.set_params(prec="c128")
+            _FP64_SOLUTIONS[key] = G.solve(b, rtol=rtol, maxit=200)[0].cpu()
+            G.set_params(prec=prm["prec"])
+        x64 = _FP64_SOLUTIONS[key].cuda()
+        nrm = float(torch.linalg.vector_norm(x64))
+        st0["solution_rel_err_vs_fp64"] = float(torch.linalg.vector_norm(x0 - x64)) / nrm
+        st1["solution_rel_err_vs_fp64"] = float(torch.linalg.vector_norm(x1 - x64)) / nrm
         rows.append(dict(seed=s, plain=st0, learned=st1))
         G.close()
     return rows
