@@ -457,13 +457,14 @@ __device__ __forceinline__ void x2_step_rows(const float2 *__restrict__ src, flo
             cen = dn[j];
         }
 #pragma unroll
-        for (int j = 0; j < CH; ++j)
+        for (int j = 0; j < CH; ++j) {
             if (SPLIT) {
                 dst[x2_cell<true, PX, BXH>(r0 + c + j, tx, 0)] = make_float2(o[j].x, o[j].y);
                 dst[x2_cell<true, PX, BXH>(r0 + c + j, tx, 1)] = make_float2(o[j].z, o[j].w);
             } else {
                 *reinterpret_cast<float4 *>(dst + (r0 + c + j + 1) * PX + cx0 + 2) = o[j];
             }
+        }
     }
 }
 
@@ -573,6 +574,7 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
     __syncthreads();
     bool alive = true;
     for (int pass = 0; pass < a.npass && alive; ++pass) {
+        const bool early_pub = pass < a.npass - 1 && !(a.w && ((pass + 1) % a.pass_per_sub) == 0);
 #pragma unroll 1
         for (int s = 0; s < K; ++s) {
             const float2 *src = (s & 1) ? b1 : b0;
@@ -600,6 +602,19 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
                     }
                 }
             }
+            if (s == K - 1 && early_pub) {
+                // publish the strips from this thread's own new cells (written by it
+                // above) before the step's barrier, so the global stores are in flight
+                S *ex = (pass & 1) ? ex1 : ex0;
+#pragma unroll 1
+                for (int r = 0; r < R; ++r) {
+                    const int ry = r0 + r;
+#pragma unroll
+                    for (int l = 0; l < 2; ++l)
+                        if ((stripmask[l] >> r) & 1u)
+                            St<S>::st(ex, (int64_t)(gy0 + ry) * n0 + gx[l], dst[x2_cell<SPLIT, PX, BXH>(ry, tx, l)]);
+                }
+            }
             __syncthreads();
         }
         if (a.w && ((pass + 1) % a.pass_per_sub) == 0) {
@@ -618,13 +633,15 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
         }
         if (pass == a.npass - 1) break;
         S *ex = (pass & 1) ? ex1 : ex0;
+        if (!early_pub) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int ry = grp * R + r;
+            for (int r = 0; r < R; ++r) {
+                const int ry = grp * R + r;
 #pragma unroll
-            for (int l = 0; l < 2; ++l)
-                if ((stripmask[l] >> r) & 1u)
-                    St<S>::st(ex, (int64_t)(gy0 + ry) * n0 + gx[l], b0[x2_cell<SPLIT, PX, BXH>(ry, tx, l)]);
+                for (int l = 0; l < 2; ++l)
+                    if ((stripmask[l] >> r) & 1u)
+                        St<S>::st(ex, (int64_t)(gy0 + ry) * n0 + gx[l], b0[x2_cell<SPLIT, PX, BXH>(ry, tx, l)]);
+            }
         }
         alive = neighbour_sync(a.bar, bx, by, a.ntx, a.nty, (unsigned)(pass + 1));
         if (!alive) break;
