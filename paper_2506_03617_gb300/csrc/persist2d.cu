@@ -102,11 +102,13 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
     return v;
 }
 
+// entry_barrier = false when the caller has just passed a CTA barrier after its
+// last store of the strips (nothing to order again).
 __device__ __forceinline__ bool neighbour_sync(unsigned *bar, int bx, int by, int ntx, int nty,
-                                               unsigned epoch)
+                                               unsigned epoch, bool entry_barrier = true)
 {
     __shared__ int s_ok2;
-    __syncthreads();
+    if (entry_barrier) __syncthreads();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         const unsigned *flags = bar + 4;
@@ -643,7 +645,8 @@ __global__ void __launch_bounds__(BXH *BG, 1) k_persist2d_x2(PersistArgs a, cons
                         St<S>::st(ex, (int64_t)(gy0 + ry) * n0 + gx[l], b0[x2_cell<SPLIT, PX, BXH>(ry, tx, l)]);
             }
         }
-        alive = neighbour_sync(a.bar, bx, by, a.ntx, a.nty, (unsigned)(pass + 1));
+        // after an early publish the last step's barrier already ordered the strips
+        alive = neighbour_sync(a.bar, bx, by, a.ntx, a.nty, (unsigned)(pass + 1), !early_pub);
         if (!alive) break;
         const bool sub_end = ((pass + 1) % a.pass_per_sub) == 0;
 #pragma unroll
