@@ -17,11 +17,12 @@ def _declared():
     return names
 
 
-def test_header_declares_the_survey_entry_points():
+def test_header_declares_the_core_entry_points():
     names = _declared()
     for required in ["mxp_create", "mxp_set_params", "mxp_apply_operator", "mxp_apply_matexpre",
                      "mxp_solve", "mxp_solve_batch", "mxp_destroy", "mxp_status_string",
-                     "mxp_last_error"]:
+                     "mxp_last_error", "mxp_apply_phi", "mxp_create_slab", "mxp_horner_step",
+                     "mxp_vec_mdot", "mxp_vec_combine", "mxp_apply_phi_noalloc"]:
         assert required in names
 
 
