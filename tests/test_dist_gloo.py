@@ -308,3 +308,35 @@ def test_slab_decomposed_solve_matches_one_domain():
         assert (st["outer_iters"], st["inner_iters_total"]) == (st1["outer_iters"], st1["inner_iters_total"])
     assert np.linalg.norm(x2 - x1) / np.linalg.norm(x1) < 1e-9
     assert np.linalg.norm(b - P.apply(x2)) / np.linalg.norm(b) <= 1.000001e-6
+
+
+def test_slab_least_squares_matches_numpy():
+    """The host least squares of the slab solver (Givens rotations applied
+    column by column to the (R + 1) x R Hessenberg matrix): residual estimates
+    and solutions equal numpy's least-squares solution of min ||beta e1 - H y||
+    for every leading size."""
+    from paper_2506_03617_gb300 import dist as D
+    rng = np.random.default_rng(5)
+    R = 12
+    H = np.triu(rng.standard_normal((R + 1, R)) + 1j * rng.standard_normal((R + 1, R)), -1)
+    beta = 2.5
+    lsq = D._Lsq(R, beta)
+    for j in range(R):
+        est = lsq.add(j, H[:j + 1, j], H[j + 1, j])
+        e1 = np.zeros(j + 2, dtype=np.complex128)
+        e1[0] = beta
+        y_ref = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+        res_ref = np.linalg.norm(e1 - H[:j + 2, :j + 1] @ y_ref)
+        assert abs(est - res_ref) <= 1e-12 * beta
+        assert np.max(np.abs(lsq.solve(j + 1) - y_ref)) <= 1e-10 * np.max(np.abs(y_ref))
+
+
+def test_givens_zeroes_the_second_entry():
+    from paper_2506_03617_gb300 import dist as D
+    for a, b in [(1 + 2j, 3 - 1j), (0j, 2 + 1j), (1.5 + 0j, 0j), (-2j, 1e-3 + 4j)]:
+        c, s = D._givens(a, b)
+        G = np.array([[c, s], [-np.conj(s), c]])
+        v = G @ np.array([a, b])
+        assert abs(v[1]) <= 1e-14 * (abs(a) + abs(b))
+        assert abs(abs(v[0]) - np.hypot(abs(a), abs(b))) <= 1e-14 * (abs(a) + abs(b))
+        assert np.allclose(G.conj().T @ G, np.eye(2), atol=1e-14)
