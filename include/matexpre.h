@@ -88,9 +88,10 @@ typedef struct {
  *  persist_cfg  persistent exp-action kernel (2D, MXP_C64 / MXP_BF16S): one
  *             cooperative launch per exp action with the grid held on chip;
  *             -1 = used when the autotuner finds it faster, -2 = never,
- *             >= 0 = force that configuration when the grid fits the GPU and,
- *             for a problem with sound-hard / absorbing faces, the configuration
- *             adds face terms (otherwise the per-point sweep is used)
+ *             0 .. mxp_num_persist_configs() - 1 = force that configuration when
+ *             the grid fits the GPU and, for a problem with sound-hard / absorbing
+ *             faces, the configuration adds face terms (otherwise the per-point
+ *             sweep is used)
  *  precond    preconditioner of mxp_apply_matexpre and mxp_solve: 0 = Algorithm 1
  *             (default); 1 = the truncated Neumann series of Sec. 3.2,
  *             P_N r = (sum_{n=0}^{N} exp(i t A_s)^n) psi_1(i t A_s) r (constant -i t
