@@ -8,6 +8,7 @@ import os
 import socket
 
 import numpy as np
+import pytest
 import torch.multiprocessing as mp
 
 from paper_2506_03617_gb300 import inputs as I
@@ -340,3 +341,37 @@ def test_givens_zeroes_the_second_entry():
         assert abs(v[1]) <= 1e-14 * (abs(a) + abs(b))
         assert abs(abs(v[0]) - np.hypot(abs(a), abs(b))) <= 1e-14 * (abs(a) + abs(b))
         assert np.allclose(G.conj().T @ G, np.eye(2), atol=1e-14)
+
+
+@pytest.mark.parametrize("which,world,halo", [(0, 2, 2), (1, 3, 4), (2, 2, 3)])
+def test_slab_phi_actions_match_the_oracle(which, world, halo):
+    """exp, psi_1 and psi_2 actions of the slab driver (augmented scalar rows for
+    the psi actions, halo exchange every `halo` Horner steps) on slabs of one
+    grid held by one process, against the oracle's actions on the whole grid."""
+    import torch
+    import oracle
+    from _slab_oracle import OracleSlab
+    from paper_2506_03617_gb300 import dist as D
+    from paper_2506_03617_gb300 import native as N
+    g = I.Grid(2, (18, 22), 4)
+    c = I.layered_grf(g, seed=I.SEED_BASE + 9600, corr_cells=3.0)
+    p = I.paper_params(g, c, ppw=10.0, t_over_h2=10.0)
+    P = oracle.Problem.from_grid(g, c, p)
+    S, m = N.taylor_plan(1.2 * P.norm_inf_tA(True), 1e-14, 4.0, 1)   # margin for the augmented rows
+    params = dict(t=p.t, fprtol=p.fprtol, inner_restart=30, inner_maxit=100, inner_fixed=0, precond=0,
+                  neumann_n=0)
+    rows, row = g.n[-1], g.n[0]
+    bounds = D.slab_bounds(rows, world)
+    ext = [D.slab_extended(bounds, k, halo, rows) for k in range(world)]
+    slabs = [OracleSlab(P, g, e0, e1, params, [(0.0, S, m)] * 3) for e0, e1 in ext]
+    x = I.random_complex(g.n_total, 33)
+    xs = [torch.from_numpy(np.ascontiguousarray(x[e0 * row:e1 * row])) for e0, e1 in ext]
+    outs = [torch.zeros_like(v) for v in xs]
+    solver = D.SlabSolver(slabs, [(r0 - e0, r1 - e0) for (e0, _), (r0, r1) in zip(ext, bounds)],
+                          D.LocalSlabExchange(bounds, halo, row, rows), None, halo)
+    solver.phi(which, xs, outs)
+    got = np.zeros_like(x)
+    for (e0, _), (r0, r1), v in zip(ext, bounds, outs):
+        got[r0 * row:r1 * row] = v.numpy()[(r0 - e0) * row:(r1 - e0) * row]
+    ref = P.phi(which, x)[0]
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-10
