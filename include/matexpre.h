@@ -200,7 +200,8 @@ mxp_status mxp_get_plan(const mxp_problem *prob, int which, double *mu, int *S, 
  * Synchronises the stream.
  *
  * mxp_vec_combine: y = beta y + sum_{i < k} coef_i V_i, complex scalars as
- * {re, im} (beta[2], coef_host[2k]), 0 <= k <= 64; y must not alias a V_i.
+ * {re, im} (beta[2], coef_host[2k]), 0 <= k <= 64; with beta = 0, y is not read
+ * (it may hold anything, NaN included); y must not alias a V_i.
  * Asynchronous (the coefficients are copied before the call returns).
  * MXP_EINVAL for out-of-range k, rows or ldv. */
 mxp_status mxp_vec_mdot(mxp_problem *prob, const void *V_dev, int64_t ldv, int k, const void *w_dev,

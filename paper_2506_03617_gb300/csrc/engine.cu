@@ -2286,7 +2286,10 @@ mxp_status mxp_vec_combine(mxp_problem *P, void *y_dev, const double *beta, cons
     DeviceGuard guard(P->device);
     CKS(ensure_vec(P));
     const int64_t n = P->ntot;
-    if (!(beta[0] == 1.0 && beta[1] == 0.0)) krylov_scale((double2 *)y_dev, make_double2(beta[0], beta[1]), n, P->stream);
+    if (beta[0] == 0.0 && beta[1] == 0.0)
+        CK(cudaMemsetAsync(y_dev, 0, (size_t)n * sizeof(double2), P->stream));   // y is not read
+    else if (!(beta[0] == 1.0 && beta[1] == 0.0))
+        krylov_scale((double2 *)y_dev, make_double2(beta[0], beta[1]), n, P->stream);
     if (k > 0) {
         CK(cudaMemcpyAsync(P->vec_dev + 64, coef_host, (size_t)k * sizeof(double2), cudaMemcpyHostToDevice, P->stream));
         krylov_maxpy((double2 *)y_dev, (const double2 *)V_dev, ldv, k, P->vec_dev + 64, 1.0, n, P->stream);
