@@ -375,3 +375,47 @@ def test_slab_phi_actions_match_the_oracle(which, world, halo):
         got[r0 * row:r1 * row] = v.numpy()[(r0 - e0) * row:(r1 - e0) * row]
     ref = P.phi(which, x)[0]
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-10
+
+
+@pytest.mark.parametrize("precond", [1, 2])
+def test_slab_solver_other_preconditioners_match_one_domain(precond):
+    """The slab driver with the truncated Neumann series (precond 1, N = 2) and
+    with the second inverse formula (precond 2) on three CPU slabs in one process
+    takes the one-domain run's iteration counts and solution, and meets rtol in
+    the oracle's true residual."""
+    import torch
+    import oracle
+    from _slab_oracle import OracleSlab
+    from paper_2506_03617_gb300 import dist as D
+    from paper_2506_03617_gb300 import native as N
+    g = I.Grid(2, (16, 20), 4)
+    c = I.layered_grf(g, seed=I.SEED_BASE + 9700, corr_cells=3.0)
+    p = I.paper_params(g, c, ppw=10.0, t_over_h2=10.0)
+    P = oracle.Problem.from_grid(g, c, p)
+    S, m = N.taylor_plan(1.2 * P.norm_inf_tA(True), 1e-12, 4.0, 1)
+    params = dict(t=p.t, fprtol=p.fprtol, inner_restart=30, inner_maxit=200, inner_fixed=0, precond=precond,
+                  neumann_n=2)
+    b = I.rhs_from_source(I.gaussian_source(g)).ravel()
+    rows, row = g.n[-1], g.n[0]
+
+    def run(world, halo):
+        bounds = D.slab_bounds(rows, world)
+        ext = [D.slab_extended(bounds, k, halo, rows) for k in range(world)]
+        slabs = [OracleSlab(P, g, e0, e1, params, [(0.0, S, m)] * 3) for e0, e1 in ext]
+        bs = [torch.from_numpy(np.ascontiguousarray(b[e0 * row:e1 * row])) for e0, e1 in ext]
+        xs = [torch.zeros_like(v) for v in bs]
+        ex = D.LocalSlabExchange(bounds, halo, row, rows) if world > 1 else (lambda vs: None)
+        solver = D.SlabSolver(slabs, [(r0 - e0, r1 - e0) for (e0, _), (r0, r1) in zip(ext, bounds)], ex, None,
+                              halo)
+        st = solver.solve(bs, xs, rtol=1e-6, restart=30, maxit=80)
+        x = np.zeros_like(b)
+        for (e0, _), (r0, r1), v in zip(ext, bounds, xs):
+            x[r0 * row:r1 * row] = v.numpy()[(r0 - e0) * row:(r1 - e0) * row]
+        return x, st
+
+    x1, st1 = run(1, 3)
+    x3, st3 = run(3, 3)
+    assert st1["converged"] and st3["converged"]
+    assert (st3["outer_iters"], st3["inner_iters_total"]) == (st1["outer_iters"], st1["inner_iters_total"])
+    assert np.linalg.norm(x3 - x1) / np.linalg.norm(x1) < 1e-9
+    assert np.linalg.norm(b - P.apply(x3)) / np.linalg.norm(b) <= 1.000001e-6
